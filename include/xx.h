@@ -1,0 +1,205 @@
+/*
+ * xx.h -- C ABI of the GB300 plane-wave Fock exchange library (libxx.so).
+ *
+ * The library applies the exact-exchange (Fock) operator V_x of a block of
+ * occupied orbitals to a block of target orbitals in a plane-wave basis, and
+ * reduces the exchange energy E_x, following Hutchinson & Widom, "VASP on a
+ * GPU" (Sec. "Our Implementation", Eq. 2: the four nested loops over k, q and
+ * two band indices, whose inner band loops run on the GPU).  One GPU, one
+ * process; every call is asynchronous on the caller's CUDA stream.
+ *
+ * Units and conventions (Hartree atomic units, lengths in bohr):
+ *   - lattice: 9 doubles, rows a1, a2, a3.  Reciprocal rows b_i with
+ *     a_i . b_j = 2 pi delta_ij.  Omega = |a1 . (a2 x a3)|.
+ *   - k-points: fractional coordinates kfrac[k][3] (reciprocal basis).  The
+ *     same mesh serves as target k and occupied q; weights are 1/N_k.
+ *   - basis of k: Miller indices miller[k][g][3], g < npw[k], of plane waves
+ *     exp(i (G + k).r); rows g >= npw[k] are padding and ignored.
+ *   - orbitals: complex128 coefficients c[k][b][g] (interleaved re, im) of the
+ *     cell-periodic part u_kb(r) = Omega^(-1/2) sum_G c_kb(G) exp(i G.r).
+ *   - occupations w[k][b]: per spin, in [0, 1]; spin-paired (s = 2).
+ *   - FFT grid N1 x N2 x N3, index p = i1 + N1 (i2 + N2 i3).
+ *
+ * Operator (per target (k, a)), exactly as the paper's loops state it:
+ *   rho_aj(r) = conj(u_qj(r)) u_ka(r)
+ *   W_aj(r)   = sum_G v(k - q + G) rhohat_aj(G) exp(i G.r),
+ *               rhohat(G) = (1/N) sum_p rho(r_p) exp(-i G.r_p)
+ *   (V_x u_ka)(r) = -sum_{q,j} (w_qj / N_k) u_qj(r) W_aj(r)
+ *   (V_x c)_ka(G) = (sqrt(Omega)/N) sum_p exp(-i G.r_p) (V_x u_ka)(r_p), G in the basis of k
+ *   E_x = (s/2) (1/N_k) sum_{k,a} w_ka Re <c_ka | V_x c_ka>
+ * Kernels: XX_KERNEL_HSE is the screened (erfc(mu r)/r, HSE-type) interaction
+ *   v(g) = 4 pi / |g|^2 (1 - exp(-|g|^2 / (4 mu^2))), v(0) = pi / mu^2;
+ * XX_KERNEL_COULOMB_G0_DROPPED is 4 pi / |g|^2 with the g = 0 term dropped.
+ * The library returns pure exchange: a hybrid functional's mixing fraction is
+ * the caller's to apply.
+ *
+ * Grids: every axis must hold the codensity without wrap-around, i.e.
+ * N_i >= 4 n_i + 1 where n_i is the largest |Miller index| along axis i over
+ * all basis sets (the paper's "FFTs performed without wrap-around errors");
+ * otherwise xx_create returns XX_ERR_GRID_ALIASING.  Supported axis lengths:
+ * 24, 32, 40, 48, 60, 64, 72, 80, 96, equal on all three axes.
+ *
+ * Ownership: the caller owns every input and output buffer (device memory
+ * unless stated otherwise).  The plan owns its derived tables and workspace,
+ * allocated with cudaMalloc on the current device at first use and released
+ * by xx_destroy.  A plan may be used from one host thread at a time.
+ *
+ * Errors: every entry point returns an int status (XX_OK = 0, negative on
+ * failure) and never throws.  Argument checks happen before any GPU work.
+ * Device-side problems (an inconsistent Miller index, say) set a flag in the
+ * plan that xx_sync reports.
+ */
+#ifndef XX_H
+#define XX_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define XX_OK 0
+#define XX_ERR_INVALID_ARGUMENT (-1)
+#define XX_ERR_UNSUPPORTED_GRID (-2)
+#define XX_ERR_GRID_ALIASING (-3)
+#define XX_ERR_OUT_OF_MEMORY (-4)
+#define XX_ERR_CUDA (-5)
+#define XX_ERR_DEVICE_FLAG (-6)
+#define XX_ERR_TIMEOUT (-7)
+#define XX_ERR_NO_DEVICE (-8)
+
+#define XX_FP32_MIXED 0   /* FFTs and pointwise products in FP32, sums in FP64 */
+#define XX_FP64 1         /* every step in FP64 */
+
+#define XX_KERNEL_HSE 0
+#define XX_KERNEL_COULOMB_G0_DROPPED 1
+
+typedef struct xx_plan_s *xx_plan;
+
+/* Plan facts, filled by xx_plan_info. */
+typedef struct {
+  int grid[3];              /* FFT grid */
+  int n_max[3];             /* largest |Miller index| per axis */
+  int pruned[3];            /* kept codensity frequencies per axis, 4 n_max + 1 */
+  int nk;                   /* k-points */
+  int npw_max;
+  int precision;            /* XX_FP32_MIXED or XX_FP64 */
+  int targets_per_batch;    /* band-pair batch shape (NSIM analogue) */
+  int occupied_per_batch;
+  double omega;             /* cell volume, bohr^3 */
+  size_t workspace_bytes;   /* device workspace held now */
+  size_t peak_workspace_bytes;
+  long long kernel_launches; /* kernels launched by this plan so far */
+} xx_info;
+
+/*
+ * Create a plan (the paper's per-run library context, created at the start of
+ * the run).  lattice[9], grid[3], kfrac[nk*3], npw[nk] and
+ * miller[nk*npw_max*3] are HOST arrays, copied into the plan.  kernel_type is
+ * XX_KERNEL_HSE (mu > 0, bohr^-1) or XX_KERNEL_COULOMB_G0_DROPPED (mu
+ * ignored).  precision is XX_FP32_MIXED or XX_FP64.  workspace_cap bounds the
+ * band-pair intermediate in bytes (0 = 2 GiB); it sets how many band pairs are
+ * processed per batch (the paper's NSIM control of GPU memory).
+ * Returns XX_ERR_INVALID_ARGUMENT, XX_ERR_UNSUPPORTED_GRID, XX_ERR_GRID_ALIASING,
+ * XX_ERR_NO_DEVICE, XX_ERR_OUT_OF_MEMORY or XX_OK; *out is NULL on failure.
+ */
+int xx_create(xx_plan *out, const double *lattice, const int *grid, int nk, const double *kfrac,
+              const int *npw, int npw_max, const int *miller, int kernel_type, double mu,
+              int precision, size_t workspace_cap);
+
+/* Release the plan and its device memory (the paper's context destruction).
+ * Synchronises the device first.  NULL is accepted. */
+int xx_destroy(xx_plan plan);
+
+/*
+ * vx_out[k][a][g] = (V_x c_tgt)_ka(G) for every k and target a.
+ *   c_occ: device complex128 [nk][ld_occ][npw_max]; the occupied orbitals are
+ *          bands 0..n_occ-1 of each k (ld_occ >= n_occ band slots per k; 0
+ *          means n_occ).  When c_occ == c_tgt and ld_occ == n_tgt the
+ *          occupied grids are taken from the target grids (computed once).
+ *   w_occ: device double [nk][n_occ] per-spin occupations.
+ *   c_tgt: device complex128 [nk][n_tgt][npw_max].
+ *   vx_out: device complex128 [nk][n_tgt][npw_max], caller-allocated, must not
+ *          alias an input; padding rows are written as zero.
+ *   stream: a cudaStream_t (NULL = legacy default stream).
+ */
+int xx_apply(xx_plan plan, const void *c_occ, int ld_occ, const double *w_occ, int n_occ,
+             const void *c_tgt, int n_tgt, void *vx_out, void *stream);
+
+/*
+ * Same as xx_apply for the target k-points k_first .. k_first + k_count - 1
+ * only (the occupied orbitals still span every q of the mesh): c_tgt and
+ * vx_out hold [k_count][n_tgt][npw_max].  Target k-points are independent, so
+ * disjoint ranges may run on different GPUs (each needs every occupied orbital).
+ */
+int xx_apply_range(xx_plan plan, int k_first, int k_count, const void *c_occ, int ld_occ,
+                   const double *w_occ, int n_occ, const void *c_tgt, int n_tgt, void *vx_out,
+                   void *stream);
+
+/*
+ * E_x of the targets: runs xx_apply into vx_out (device, required) and then
+ * the deterministic FP64 reduction of (s/2)(1/N_k) sum w_tgt <c_tgt|V_x c_tgt>.
+ *   w_tgt: device double [nk][n_tgt].
+ *   ex_out: device double[2] = {Re E_x, Im E_x}; the imaginary part is a
+ *          diagnostic that vanishes for a Hermitian V_x.
+ */
+int xx_energy(xx_plan plan, const void *c_occ, int ld_occ, const double *w_occ, int n_occ,
+              const void *c_tgt, const double *w_tgt, int n_tgt, void *vx_out, double *ex_out,
+              void *stream);
+
+/* The share of E_x from target k-points k_first .. k_first + k_count - 1 (the
+ * 1/N_k of the full mesh is kept, so the shares of disjoint ranges add up to
+ * E_x); c_tgt, w_tgt and vx_out hold those k-points only. */
+int xx_energy_range(xx_plan plan, int k_first, int k_count, const void *c_occ, int ld_occ,
+                    const double *w_occ, int n_occ, const void *c_tgt, const double *w_tgt,
+                    int n_tgt, void *vx_out, double *ex_out, void *stream);
+
+/* The reduction alone: ex_out[2] from a V_x c already in vx (device). */
+int xx_energy_from_vx(xx_plan plan, const void *c_tgt, const double *w_tgt, int n_tgt,
+                      const void *vx, double *ex_out, void *stream);
+
+/* The reduction alone over target k-points k_first .. k_first + k_count - 1. */
+int xx_energy_from_vx_range(xx_plan plan, int k_first, int k_count, const void *c_tgt,
+                            const double *w_tgt, int n_tgt, const void *vx, double *ex_out,
+                            void *stream);
+
+/*
+ * Gradients of E_x[c] where the same orbitals c (device complex128
+ * [nk][n_b][npw_max]) with occupations w (device double [nk][n_b]) are both the
+ * occupied set and the targets.
+ *   vx: V_x c from a previous xx_apply/xx_energy with these inputs (device), or
+ *       NULL to recompute it inside this call.
+ *   grad_ex: upstream scalar dL/dE_x.
+ *   dc_out (device complex128 [nk][n_b][npw_max], or NULL): the Wirtinger
+ *       derivative grad_ex * dE_x/dc* = grad_ex * (s w_kb / N_k) (V_x c)_kb.
+ *   dmu_out (device double[1], or NULL): grad_ex * dE_x/dmu, with
+ *       dv/dmu = -(2 pi / mu^3) exp(-|g|^2 / (4 mu^2)); it recomputes every pair
+ *       codensity (forward transforms only) and stores no pair grid.
+ *       Requires XX_KERNEL_HSE.
+ */
+int xx_apply_backward(xx_plan plan, const void *c, const double *w, int n_b, const void *vx,
+                      double grad_ex, void *dc_out, double *dmu_out, void *stream);
+
+/*
+ * Wait for the plan's work on stream with a time limit (seconds, <= 0 waits
+ * without limit), then report the device error flag.  Returns XX_OK,
+ * XX_ERR_TIMEOUT (the stream is still busy; nothing was cancelled),
+ * XX_ERR_DEVICE_FLAG (and clears the flag) or XX_ERR_CUDA.
+ */
+int xx_sync(xx_plan plan, void *stream, double timeout_s);
+
+/* Override the band-pair batch shape (targets x occupied per batch); 0 keeps
+ * the automatic choice.  Takes effect at the next call. */
+int xx_set_batch(xx_plan plan, int targets_per_batch, int occupied_per_batch);
+
+/* Fill *info with the plan's facts. */
+int xx_plan_info(xx_plan plan, xx_info *info);
+
+/* Static description of a status code. */
+const char *xx_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XX_H */

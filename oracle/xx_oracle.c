@@ -266,8 +266,8 @@ int oracle_apply(const double lattice[9], const int grid[3], int nk, const doubl
     memset(vx_out, 0, sizeof(cplx) * (size_t)n_sel * npw_max);
 
     cplx *u_occ = malloc(sizeof(cplx) * ntot * (size_t)n_occ);
-    cplx *u_a = malloc(sizeof(cplx) * ntot);
-    cplx *acc = malloc(sizeof(cplx) * ntot);
+    cplx *u_a = malloc(sizeof(cplx) * ntot * (size_t)n_sel);
+    cplx *acc = malloc(sizeof(cplx) * ntot * (size_t)n_sel);
     cplx *rho = malloc(sizeof(cplx) * ntot);
     double *v = malloc(sizeof(double) * ntot);
 
@@ -277,36 +277,40 @@ int oracle_apply(const double lattice[9], const int grid[3], int nk, const doubl
         if (!any) continue;
         for (int t = 0; t < n_sel; ++t) {
             if (selk[t] != k) continue;
-            const int a = sela[t];
             oracle_sphere_to_grid(lattice, grid, npw[k], miller + (long)k * npw_max * 3,
-                                  c_tgt + ((long)k * n_tgt + a) * npw_max, u_a);
-            memset(acc, 0, sizeof(cplx) * ntot);
-            for (int q = 0; q < nk; ++q) {
-                for (int j = 0; j < n_occ; ++j)
-                    oracle_sphere_to_grid(lattice, grid, npw[q],
-                                          miller + (long)q * npw_max * 3,
-                                          c_occ + ((long)q * n_occ + j) * npw_max,
-                                          u_occ + ntot * j);
-                double d[3] = {kfrac[3 * k] - kfrac[3 * q], kfrac[3 * k + 1] - kfrac[3 * q + 1],
-                               kfrac[3 * k + 2] - kfrac[3 * q + 2]};
-                oracle_kernel_grid(lattice, grid, d, kernel, mu, 0, v);
+                                  c_tgt + ((long)k * n_tgt + sela[t]) * npw_max, u_a + ntot * t);
+            memset(acc + ntot * t, 0, sizeof(cplx) * ntot);
+        }
+        for (int q = 0; q < nk; ++q) {
+            for (int j = 0; j < n_occ; ++j)
+                oracle_sphere_to_grid(lattice, grid, npw[q], miller + (long)q * npw_max * 3,
+                                      c_occ + ((long)q * n_occ + j) * npw_max, u_occ + ntot * j);
+            double d[3] = {kfrac[3 * k] - kfrac[3 * q], kfrac[3 * k + 1] - kfrac[3 * q + 1],
+                           kfrac[3 * k + 2] - kfrac[3 * q + 2]};
+            oracle_kernel_grid(lattice, grid, d, kernel, mu, 0, v);
+            for (int t = 0; t < n_sel; ++t) {
+                if (selk[t] != k) continue;
+                const cplx *ua = u_a + ntot * t;
+                cplx *acct = acc + ntot * t;
                 for (int j = 0; j < n_occ; ++j) {
                     const double wq = w_occ[(long)q * n_occ + j];
                     const cplx *uj = u_occ + ntot * j;
 #pragma omp parallel for schedule(static)
-                    for (long p = 0; p < ntot; ++p) rho[p] = conj(uj[p]) * u_a[p];
+                    for (long p = 0; p < ntot; ++p) rho[p] = conj(uj[p]) * ua[p];
                     oracle_fft3d(rho, grid[0], grid[1], grid[2], -1);
 #pragma omp parallel for schedule(static)
                     for (long p = 0; p < ntot; ++p) rho[p] *= v[p] / (double)ntot;
                     oracle_fft3d(rho, grid[0], grid[1], grid[2], +1);
                     const double f = -wq / (double)nk;
 #pragma omp parallel for schedule(static)
-                    for (long p = 0; p < ntot; ++p) acc[p] += f * uj[p] * rho[p];
+                    for (long p = 0; p < ntot; ++p) acct[p] += f * uj[p] * rho[p];
                 }
             }
-            oracle_grid_to_sphere(lattice, grid, npw[k], miller + (long)k * npw_max * 3, acc,
-                                  vx_out + (long)t * npw_max);
         }
+        for (int t = 0; t < n_sel; ++t)
+            if (selk[t] == k)
+                oracle_grid_to_sphere(lattice, grid, npw[k], miller + (long)k * npw_max * 3,
+                                      acc + ntot * t, vx_out + (long)t * npw_max);
     }
     free(u_occ); free(u_a); free(acc); free(rho); free(v); free(selk); free(sela);
     return 0;

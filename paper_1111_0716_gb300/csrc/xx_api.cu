@@ -1,0 +1,819 @@
+// xx_api.cu -- C ABI of the Fock-exchange library: plan creation, workspace,
+// the host loops over k, q and band-pair batches, and the FP64 reductions.
+//
+// Host loop structure (Hutchinson & Widom, Sec. "Our Implementation": outer
+// loops over two k-points on the host, inner band loops on the GPU, the
+// innermost band loop multiplexed into batches whose size bounds GPU memory):
+//   sphere -> grid for every target and occupied orbital (once each)
+//   for k: zero the FP64 accumulators of the targets of k
+//     for q: kernel table v(k - q + G)
+//       for each (target batch, occupied batch): pass A, pass B, pass C
+//     grid -> sphere of the accumulators into V_x c
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <ctime>
+#include <new>
+#include <vector>
+
+#include "../../include/xx.h"
+#include "xx_launch.cuh"
+
+namespace xx {
+const KernelTable* kernel_table_24();
+const KernelTable* kernel_table_32();
+const KernelTable* kernel_table_40();
+const KernelTable* kernel_table_48();
+const KernelTable* kernel_table_60();
+const KernelTable* kernel_table_64();
+const KernelTable* kernel_table_72();
+const KernelTable* kernel_table_80();
+const KernelTable* kernel_table_96();
+
+const KernelTable* kernel_table(int n) {
+  switch (n) {
+    case 24: return kernel_table_24();
+    case 32: return kernel_table_32();
+    case 40: return kernel_table_40();
+    case 48: return kernel_table_48();
+    case 60: return kernel_table_60();
+    case 64: return kernel_table_64();
+    case 72: return kernel_table_72();
+    case 80: return kernel_table_80();
+    case 96: return kernel_table_96();
+    default: return nullptr;
+  }
+}
+
+constexpr int kRedThreads = 256;
+constexpr double kSpin = 2.0;   // spin-paired: s = 2
+
+// out[b][g] = scale * box[b][m3][m2][m1] for g < npw, zero padding up to npw_max
+__global__ void k_g2s_gather(GridArgs g) {
+  const long long total = (long long)g.nb * g.npw_max;
+  const double2* box = reinterpret_cast<const double2*>(g.box);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(i / g.npw_max), ig = (int)(i % g.npw_max);
+    double2 v = make_double2(0.0, 0.0);
+    if (ig < g.npw) {
+      const int* m = g.miller + 3 * ig;
+      const int x = m[0] + g.n1, y = m[1] + g.n2, z = m[2] + g.n3;
+      if (x < 0 || x >= g.Q1 || y < 0 || y >= g.Q2 || z < 0 || z >= g.Q3) {
+        atomicOr(g.err, 2);
+      } else {
+        const double2 s = box[(((long long)b * g.Q3 + z) * g.Q2 + y) * g.Q1 + x];
+        v = make_double2(g.scale * s.x, g.scale * s.y);
+      }
+    }
+    g.out[i] = v;
+  }
+}
+
+// dots[row] = sum_g conj(c[row][g]) vx[row][g], fixed-order block reduction
+__global__ void __launch_bounds__(kRedThreads) k_dot_rows(const double2* c, const double2* vx,
+                                                          const int* npw, int n_per_k, int npw_max,
+                                                          double2* dots) {
+  __shared__ double re_s[kRedThreads], im_s[kRedThreads];
+  const int row = blockIdx.x;
+  const int n = npw[row / n_per_k];
+  const double2* a = c + (long long)row * npw_max;
+  const double2* b = vx + (long long)row * npw_max;
+  double re = 0.0, im = 0.0;
+  for (int g = threadIdx.x; g < n; g += kRedThreads) {
+    const double2 x = a[g], y = b[g];
+    re += x.x * y.x + x.y * y.y;
+    im += x.x * y.y - x.y * y.x;
+  }
+  re_s[threadIdx.x] = re;
+  im_s[threadIdx.x] = im;
+  __syncthreads();
+  for (int off = kRedThreads / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      re_s[threadIdx.x] += re_s[threadIdx.x + off];
+      im_s[threadIdx.x] += im_s[threadIdx.x + off];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) dots[row] = make_double2(re_s[0], im_s[0]);
+}
+
+// ex[0..1] = scale * sum_row w[row] dots[row], one CTA, fixed order
+__global__ void __launch_bounds__(kRedThreads) k_energy(const double2* dots, const double* w,
+                                                        int nrows, double scale, double* ex) {
+  __shared__ double re_s[kRedThreads], im_s[kRedThreads];
+  double re = 0.0, im = 0.0;
+  for (int r = threadIdx.x; r < nrows; r += kRedThreads) {
+    re += w[r] * dots[r].x;
+    im += w[r] * dots[r].y;
+  }
+  re_s[threadIdx.x] = re;
+  im_s[threadIdx.x] = im;
+  __syncthreads();
+  for (int off = kRedThreads / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      re_s[threadIdx.x] += re_s[threadIdx.x + off];
+      im_s[threadIdx.x] += im_s[threadIdx.x + off];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    ex[0] = scale * re_s[0];
+    ex[1] = scale * im_s[0];
+  }
+}
+
+// acc[0] += sum over the batch's pairs of w_a w_j sum_kyb partial, one CTA, fixed order
+__global__ void __launch_bounds__(kRedThreads) k_dmu_batch(const double* partial, int P2, int TA,
+                                                           int TJ, const double* w_tgt,
+                                                           const double* w_occ, double* acc) {
+  __shared__ double s_s[kRedThreads];
+  double s = 0.0;
+  for (int p = threadIdx.x; p < TA * TJ; p += kRedThreads) {
+    double t = 0.0;
+    for (int r = 0; r < P2; ++r) t += partial[(long long)p * P2 + r];
+    s += w_tgt[p / TJ] * w_occ[p % TJ] * t;
+  }
+  s_s[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = kRedThreads / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) s_s[threadIdx.x] += s_s[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) acc[0] += s_s[0];
+}
+
+__global__ void k_scale_scalar(const double* in, double factor, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = factor * in[0];
+}
+
+// dc[row][g] = factor * w[row] * vx[row][g]
+__global__ void k_scale_rows(const double2* vx, const double* w, long long nrows, int npw_max,
+                             double factor, double2* dc) {
+  const long long total = nrows * npw_max;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double f = factor * w[i / npw_max];
+    const double2 v = vx[i];
+    dc[i] = make_double2(f * v.x, f * v.y);
+  }
+}
+
+}  // namespace xx
+
+using namespace xx;
+
+// ------------------------------------------------------------------ plan --
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct xx_plan_s {
+  int device = 0;
+  int N = 0;
+  int grid[3] = {0, 0, 0};
+  int nk = 0;
+  int npw_max = 0;
+  double lattice[9];
+  double M[9];            // reciprocal metric
+  double omega = 0.0;
+  std::vector<double> kfrac;
+  std::vector<int> npw;
+  int nmax[3] = {0, 0, 0};
+  int h[3] = {0, 0, 0};   // pruned half-widths 2 n_max
+  int kernel = 0;
+  double mu = 0.0;
+  int prec = 0;
+  size_t cap = 0;
+  int ta_user = 0, tj_user = 0;
+  int ta_last = 0, tj_last = 0;
+  const KernelTable* kt = nullptr;
+  int* d_miller = nullptr;   // [nk][npw_max][3]
+  int* d_npw = nullptr;      // [nk]
+  void* d_tw32 = nullptr;
+  void* d_tw64 = nullptr;
+  int* d_err = nullptr;
+  DevBuf u_tgt, u_occ, inter, acc, vt, dvt, box, stage, dots, partial, dmu_acc, vx_tmp;
+  size_t ws_bytes = 0, peak_bytes = 0;
+  long long launches = 0;
+};
+
+namespace {
+
+const size_t kDefaultCap = (size_t)2 << 30;
+const int kGridChunk = 32;   // orbitals per sphere<->grid launch
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return XX_OK;
+  if (e == cudaErrorMemoryAllocation) return XX_ERR_OUT_OF_MEMORY;
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return XX_ERR_NO_DEVICE;
+  return XX_ERR_CUDA;
+}
+
+int ensure(xx_plan p, DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes) return XX_OK;
+  if (b.p) {
+    cudaFree(b.p);   // synchronises with prior work that may still use it
+    p->ws_bytes -= b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return cuda_status(e);
+  }
+  b.bytes = bytes;
+  p->ws_bytes += bytes;
+  if (p->ws_bytes > p->peak_bytes) p->peak_bytes = p->ws_bytes;
+  return XX_OK;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+bool supported_n(int n) { return kernel_table(n) != nullptr; }
+
+size_t elem_bytes(const xx_plan p) { return p->prec == XX_FP64 ? 16 : 8; }
+
+long long n3(const xx_plan p) { return (long long)p->N * p->N * p->N; }
+
+int P(const xx_plan p, int ax) { return 2 * p->h[ax] + 1; }
+int Q(const xx_plan p, int ax) { return 2 * p->nmax[ax] + 1; }
+
+const KernelSet& kset(const xx_plan p) { return p->prec == XX_FP64 ? p->kt->f64 : p->kt->f32; }
+
+int launched(xx_plan p, int count) {
+  p->launches += count;
+  return cuda_status(cudaGetLastError());
+}
+
+// sphere -> grid for nb orbitals of k-point k: c[b][npw_max] -> u[b][N^3]
+int sphere_to_grid(xx_plan p, int k, const double2* c, int nb, void* u, cudaStream_t s) {
+  const size_t eb = elem_bytes(p);
+  const int Q1 = Q(p, 0), Q2 = Q(p, 1), Q3 = Q(p, 2);
+  const int chunk = nb < kGridChunk ? nb : kGridChunk;
+  int st = ensure(p, p->box, (size_t)chunk * Q1 * Q2 * Q3 * eb);
+  if (st) return st;
+  st = ensure(p, p->stage, (size_t)chunk * p->N * Q1 * Q2 * eb);
+  if (st) return st;
+  for (int b0 = 0; b0 < nb; b0 += chunk) {
+    const int cb = (nb - b0) < chunk ? (nb - b0) : chunk;
+    GridArgs g{};
+    g.c = c + (long long)b0 * p->npw_max;
+    g.miller = p->d_miller + (long long)k * p->npw_max * 3;
+    g.npw = p->npw[k];
+    g.npw_max = p->npw_max;
+    g.nb = cb;
+    g.box = p->box.p;
+    g.stage = p->stage.p;
+    g.u = (char*)u + (size_t)b0 * n3(p) * eb;
+    g.tw = p->prec == XX_FP64 ? p->d_tw64 : p->d_tw32;
+    g.n1 = p->nmax[0];
+    g.n2 = p->nmax[1];
+    g.n3 = p->nmax[2];
+    g.Q1 = Q1;
+    g.Q2 = Q2;
+    g.Q3 = Q3;
+    g.scale = 1.0 / std::sqrt(p->omega);
+    g.err = p->d_err;
+    cudaMemsetAsync(p->box.p, 0, (size_t)cb * Q1 * Q2 * Q3 * eb, s);
+    const int blocks = (int)(((long long)cb * g.npw + 255) / 256);
+    if (p->prec == XX_FP64)
+      k_s2g_scatter<double><<<blocks, 256, 0, s>>>(g);
+    else
+      k_s2g_scatter<float><<<blocks, 256, 0, s>>>(g);
+    kset(p).s2g_z(g, s);
+    kset(p).s2g_xy(g, s);
+    if ((st = launched(p, 3))) return st;
+  }
+  return XX_OK;
+}
+
+// grid -> sphere for nb FP64 grids f[b][N^3] of k-point k into out[b][npw_max]
+int grid_to_sphere(xx_plan p, int k, const double2* f, int nb, double2* out, cudaStream_t s) {
+  const int Q1 = Q(p, 0), Q2 = Q(p, 1), Q3 = Q(p, 2);
+  const int chunk = nb < kGridChunk ? nb : kGridChunk;
+  int st = ensure(p, p->box, (size_t)chunk * Q1 * Q2 * Q3 * 16);
+  if (st) return st;
+  st = ensure(p, p->stage, (size_t)chunk * p->N * Q1 * Q2 * 16);
+  if (st) return st;
+  for (int b0 = 0; b0 < nb; b0 += chunk) {
+    const int cb = (nb - b0) < chunk ? (nb - b0) : chunk;
+    GridArgs g{};
+    g.out = out + (long long)b0 * p->npw_max;
+    g.miller = p->d_miller + (long long)k * p->npw_max * 3;
+    g.npw = p->npw[k];
+    g.npw_max = p->npw_max;
+    g.nb = cb;
+    g.box = p->box.p;
+    g.stage = p->stage.p;
+    g.f = f + (long long)b0 * n3(p);
+    g.tw = p->d_tw64;
+    g.n1 = p->nmax[0];
+    g.n2 = p->nmax[1];
+    g.n3 = p->nmax[2];
+    g.Q1 = Q1;
+    g.Q2 = Q2;
+    g.Q3 = Q3;
+    g.scale = std::sqrt(p->omega) / (double)n3(p);
+    g.err = p->d_err;
+    p->kt->g2s_xy(g, s);
+    p->kt->g2s_z(g, s);
+    const int blocks = (int)(((long long)cb * p->npw_max + 255) / 256);
+    k_g2s_gather<<<blocks, 256, 0, s>>>(g);
+    if ((st = launched(p, 3))) return st;
+  }
+  return XX_OK;
+}
+
+int kernel_table_for(xx_plan p, int k, int q, bool with_dmu, cudaStream_t s) {
+  const size_t eb = p->prec == XX_FP64 ? 8 : 4;
+  const long long nbox = (long long)P(p, 0) * P(p, 1) * P(p, 2);
+  int st = ensure(p, p->vt, nbox * eb);
+  if (st) return st;
+  if (with_dmu && (st = ensure(p, p->dvt, nbox * eb))) return st;
+  VtabArgs a{};
+  std::memcpy(a.M, p->M, sizeof(a.M));
+  for (int i = 0; i < 3; ++i) a.d[i] = p->kfrac[3 * k + i] - p->kfrac[3 * q + i];
+  a.h1 = p->h[0];
+  a.h2 = p->h[1];
+  a.h3 = p->h[2];
+  a.P1 = P(p, 0);
+  a.P2 = P(p, 1);
+  a.P3 = P(p, 2);
+  a.kernel = p->kernel;
+  a.mu = p->mu;
+  a.inv_n = 1.0 / (double)n3(p);
+  a.inv_n2 = a.inv_n * a.inv_n;
+  const int blocks = (int)((nbox + 255) / 256);
+  if (p->prec == XX_FP64)
+    k_vtab<double><<<blocks, 256, 0, s>>>((double*)p->vt.p, with_dmu ? (double*)p->dvt.p : nullptr, a);
+  else
+    k_vtab<float><<<blocks, 256, 0, s>>>((float*)p->vt.p, with_dmu ? (float*)p->dvt.p : nullptr, a);
+  return launched(p, 1);
+}
+
+void batch_shape(xx_plan p, int n_tgt, int n_occ, int* TA, int* TJ) {
+  const size_t per_pair = (size_t)p->N * P(p, 1) * P(p, 0) * elem_bytes(p);
+  int ta = p->ta_user > 0 ? p->ta_user : 16;
+  int tj = p->tj_user > 0 ? p->tj_user : 32;
+  if (ta > n_tgt) ta = n_tgt;
+  if (tj > n_occ) tj = n_occ;
+  while ((size_t)ta * tj * per_pair > p->cap && tj > 1) tj = (tj + 1) / 2;
+  while ((size_t)ta * tj * per_pair > p->cap && ta > 1) ta = (ta + 1) / 2;
+  *TA = ta < 1 ? 1 : ta;
+  *TJ = tj < 1 ? 1 : tj;
+}
+
+PairArgs pair_args(xx_plan p, int TA, int TJ) {
+  PairArgs a{};
+  a.inter = p->inter.p;
+  a.vt = p->vt.p;
+  a.dvt = p->dvt.p;
+  a.partial = (double*)p->partial.p;
+  a.tw = p->prec == XX_FP64 ? p->d_tw64 : p->d_tw32;
+  a.u_tgt_stride = n3(p);
+  a.u_occ_stride = n3(p);
+  a.TA = TA;
+  a.TJ = TJ;
+  a.h1 = p->h[0];
+  a.h2 = p->h[1];
+  a.h3 = p->h[2];
+  a.P1 = P(p, 0);
+  a.P2 = P(p, 1);
+  a.P3 = P(p, 2);
+  a.coef = -1.0 / (double)p->nk;
+  return a;
+}
+
+bool bad_ptr(const void* a) { return a == nullptr; }
+
+// Grids of targets (and occupied, unless shared) for every k.
+// Targets of k-points k0..k0+kn-1 (c_tgt holds only those), occupied of every q.
+int build_grids(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, int n_occ,
+                const void* c_tgt, int n_tgt, bool shared, cudaStream_t s) {
+  const size_t eb = elem_bytes(p);
+  int st = ensure(p, p->u_tgt, (size_t)kn * n_tgt * n3(p) * eb);
+  if (st) return st;
+  for (int kk = 0; kk < kn; ++kk) {
+    st = sphere_to_grid(p, k0 + kk, (const double2*)c_tgt + (long long)kk * n_tgt * p->npw_max, n_tgt,
+                        (char*)p->u_tgt.p + (size_t)kk * n_tgt * n3(p) * eb, s);
+    if (st) return st;
+  }
+  if (!shared) {
+    if ((st = ensure(p, p->u_occ, (size_t)p->nk * n_occ * n3(p) * eb))) return st;
+    for (int q = 0; q < p->nk; ++q) {
+      st = sphere_to_grid(p, q, (const double2*)c_occ + (long long)q * ld_occ * p->npw_max, n_occ,
+                          (char*)p->u_occ.p + (size_t)q * n_occ * n3(p) * eb, s);
+      if (st) return st;
+    }
+  }
+  return XX_OK;
+}
+
+const char* grid_ptr(xx_plan p, bool shared, int q, int j, int n_occ, int n_tgt) {
+  const size_t eb = elem_bytes(p);
+  if (shared) return (const char*)p->u_tgt.p + ((size_t)q * n_tgt + j) * n3(p) * eb;
+  return (const char*)p->u_occ.p + ((size_t)q * n_occ + j) * n3(p) * eb;
+}
+
+int run_apply(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, const double* w_occ,
+              int n_occ, const void* c_tgt, int n_tgt, void* vx_out, cudaStream_t s) {
+  const bool shared = (c_occ == c_tgt && ld_occ == n_tgt && k0 == 0 && kn == p->nk);
+  int st = build_grids(p, k0, kn, c_occ, ld_occ, n_occ, c_tgt, n_tgt, shared, s);
+  if (st) return st;
+  int TA, TJ;
+  batch_shape(p, n_tgt, n_occ, &TA, &TJ);
+  p->ta_last = TA;
+  p->tj_last = TJ;
+  const size_t eb = elem_bytes(p);
+  if ((st = ensure(p, p->inter, (size_t)TA * TJ * p->N * P(p, 1) * P(p, 0) * eb))) return st;
+  if ((st = ensure(p, p->acc, (size_t)n_tgt * n3(p) * 16))) return st;
+  const KernelSet& ks = kset(p);
+  for (int kk = 0; kk < kn; ++kk) {
+    const int k = k0 + kk;
+    cudaMemsetAsync(p->acc.p, 0, (size_t)n_tgt * n3(p) * 16, s);
+    for (int q = 0; q < p->nk; ++q) {
+      if ((st = kernel_table_for(p, k, q, false, s))) return st;
+      for (int a0 = 0; a0 < n_tgt; a0 += TA) {
+        const int ta = (n_tgt - a0) < TA ? (n_tgt - a0) : TA;
+        for (int j0 = 0; j0 < n_occ; j0 += TJ) {
+          const int tj = (n_occ - j0) < TJ ? (n_occ - j0) : TJ;
+          PairArgs a = pair_args(p, ta, tj);
+          a.u_tgt = grid_ptr(p, true, kk, a0, n_occ, n_tgt);
+          a.u_occ = grid_ptr(p, shared, q, j0, n_occ, n_tgt);
+          a.acc = (double2*)p->acc.p + (long long)a0 * n3(p);
+          a.w_occ = w_occ + (long long)q * n_occ + j0;
+          ks.pass_a(a, s);
+          ks.pass_b(a, s);
+          ks.pass_c(a, s);
+          if ((st = launched(p, 3))) return st;
+        }
+      }
+    }
+    st = grid_to_sphere(p, k, (const double2*)p->acc.p, n_tgt,
+                        (double2*)vx_out + (long long)kk * n_tgt * p->npw_max, s);
+    if (st) return st;
+  }
+  return XX_OK;
+}
+
+int run_energy_reduce(xx_plan p, int k0, int kn, const void* c_tgt, const double* w_tgt, int n_tgt,
+                      const void* vx, double* ex_out, cudaStream_t s) {
+  const int rows = kn * n_tgt;
+  int st = ensure(p, p->dots, (size_t)rows * 16);
+  if (st) return st;
+  k_dot_rows<<<rows, kRedThreads, 0, s>>>((const double2*)c_tgt, (const double2*)vx, p->d_npw + k0,
+                                           n_tgt, p->npw_max, (double2*)p->dots.p);
+  k_energy<<<1, kRedThreads, 0, s>>>((const double2*)p->dots.p, w_tgt, rows, 0.5 * kSpin / p->nk, ex_out);
+  return launched(p, 2);
+}
+
+// dE/dmu accumulation: codensities recomputed (pass A) + forward z with dv/dmu (pass B')
+int run_dmu(xx_plan p, const void* c, const double* w, int n_b, double grad, double* dmu_out,
+            cudaStream_t s) {
+  int st = build_grids(p, 0, p->nk, c, n_b, n_b, c, n_b, true, s);
+  if (st) return st;
+  int TA, TJ;
+  batch_shape(p, n_b, n_b, &TA, &TJ);
+  const size_t eb = elem_bytes(p);
+  if ((st = ensure(p, p->inter, (size_t)TA * TJ * p->N * P(p, 1) * P(p, 0) * eb))) return st;
+  if ((st = ensure(p, p->partial, (size_t)TA * TJ * P(p, 1) * 8))) return st;
+  if ((st = ensure(p, p->dmu_acc, 8))) return st;
+  cudaMemsetAsync(p->dmu_acc.p, 0, 8, s);
+  const KernelSet& ks = kset(p);
+  for (int k = 0; k < p->nk; ++k)
+    for (int q = 0; q < p->nk; ++q) {
+      if ((st = kernel_table_for(p, k, q, true, s))) return st;
+      for (int a0 = 0; a0 < n_b; a0 += TA) {
+        const int ta = (n_b - a0) < TA ? (n_b - a0) : TA;
+        for (int j0 = 0; j0 < n_b; j0 += TJ) {
+          const int tj = (n_b - j0) < TJ ? (n_b - j0) : TJ;
+          PairArgs a = pair_args(p, ta, tj);
+          a.u_tgt = grid_ptr(p, true, k, a0, n_b, n_b);
+          a.u_occ = grid_ptr(p, true, q, j0, n_b, n_b);
+          ks.pass_a(a, s);
+          ks.pass_b_dmu(a, s);
+          k_dmu_batch<<<1, kRedThreads, 0, s>>>((const double*)p->partial.p, P(p, 1), ta, tj,
+                                                w + (long long)k * n_b + a0,
+                                                w + (long long)q * n_b + j0, (double*)p->dmu_acc.p);
+          if ((st = launched(p, 3))) return st;
+        }
+      }
+    }
+  const double factor = -0.5 * kSpin * p->omega / ((double)p->nk * (double)p->nk) * grad;
+  k_scale_scalar<<<1, 32, 0, s>>>((const double*)p->dmu_acc.p, factor, dmu_out);
+  return launched(p, 1);
+}
+
+bool supported_grid(const int* g) { return g[0] == g[1] && g[1] == g[2] && supported_n(g[0]); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI --
+
+extern "C" {
+
+const char* xx_status_string(int status) {
+  switch (status) {
+    case XX_OK: return "ok";
+    case XX_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case XX_ERR_UNSUPPORTED_GRID: return "unsupported FFT grid (equal axes of 24, 32, 40, 48, 60, 64, 72, 80 or 96)";
+    case XX_ERR_GRID_ALIASING: return "FFT grid too small: an axis has N < 4 n_max + 1 (codensity wrap-around)";
+    case XX_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case XX_ERR_CUDA: return "CUDA error";
+    case XX_ERR_DEVICE_FLAG: return "device-side check failed (inconsistent basis data)";
+    case XX_ERR_TIMEOUT: return "timed out waiting for the stream";
+    case XX_ERR_NO_DEVICE: return "no usable CUDA device";
+    default: return "unknown status";
+  }
+}
+
+int xx_create(xx_plan* out, const double* lattice, const int* grid, int nk, const double* kfrac,
+              const int* npw, int npw_max, const int* miller, int kernel_type, double mu,
+              int precision, size_t workspace_cap) {
+  if (!out) return XX_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  if (!lattice || !grid || !kfrac || !npw || !miller || nk < 1 || npw_max < 1)
+    return XX_ERR_INVALID_ARGUMENT;
+  if (kernel_type != XX_KERNEL_HSE && kernel_type != XX_KERNEL_COULOMB_G0_DROPPED)
+    return XX_ERR_INVALID_ARGUMENT;
+  if (kernel_type == XX_KERNEL_HSE && !(mu > 0.0 && std::isfinite(mu))) return XX_ERR_INVALID_ARGUMENT;
+  if (precision != XX_FP32_MIXED && precision != XX_FP64) return XX_ERR_INVALID_ARGUMENT;
+  for (int i = 0; i < 9; ++i)
+    if (!std::isfinite(lattice[i])) return XX_ERR_INVALID_ARGUMENT;
+  for (int i = 0; i < 3 * nk; ++i)
+    if (!std::isfinite(kfrac[i])) return XX_ERR_INVALID_ARGUMENT;
+  for (int k = 0; k < nk; ++k)
+    if (npw[k] < 1 || npw[k] > npw_max) return XX_ERR_INVALID_ARGUMENT;
+  if (!supported_grid(grid)) return XX_ERR_UNSUPPORTED_GRID;
+
+  // cell volume and reciprocal metric (b_i = 2 pi inverse-transpose rows)
+  const double* a = lattice;
+  const double c23[3] = {a[4] * a[8] - a[5] * a[7], a[5] * a[6] - a[3] * a[8], a[3] * a[7] - a[4] * a[6]};
+  const double c31[3] = {a[7] * a[2] - a[8] * a[1], a[8] * a[0] - a[6] * a[2], a[6] * a[1] - a[7] * a[0]};
+  const double c12[3] = {a[1] * a[5] - a[2] * a[4], a[2] * a[3] - a[0] * a[5], a[0] * a[4] - a[1] * a[3]};
+  const double vol = a[0] * c23[0] + a[1] * c23[1] + a[2] * c23[2];
+  if (!(std::fabs(vol) > 1e-12)) return XX_ERR_INVALID_ARGUMENT;
+
+  int nmax[3] = {0, 0, 0};
+  for (int k = 0; k < nk; ++k)
+    for (int g = 0; g < npw[k]; ++g)
+      for (int ax = 0; ax < 3; ++ax) {
+        const int m = miller[((long long)k * npw_max + g) * 3 + ax];
+        const int am = m < 0 ? -m : m;
+        if (am > 4096) return XX_ERR_INVALID_ARGUMENT;
+        if (am > nmax[ax]) nmax[ax] = am;
+      }
+  for (int ax = 0; ax < 3; ++ax)
+    if (grid[ax] < 4 * nmax[ax] + 1) return XX_ERR_GRID_ALIASING;
+
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return XX_ERR_NO_DEVICE;
+  }
+
+  xx_plan p = new (std::nothrow) xx_plan_s();
+  if (!p) return XX_ERR_OUT_OF_MEMORY;
+  cudaGetDevice(&p->device);
+  p->N = grid[0];
+  for (int i = 0; i < 3; ++i) p->grid[i] = grid[i];
+  p->nk = nk;
+  p->npw_max = npw_max;
+  std::memcpy(p->lattice, lattice, sizeof(p->lattice));
+  p->omega = std::fabs(vol);
+  double B[9];
+  const double tp = 2.0 * 3.14159265358979323846 / vol;
+  for (int i = 0; i < 3; ++i) {
+    B[0 + i] = tp * c23[i];
+    B[3 + i] = tp * c31[i];
+    B[6 + i] = tp * c12[i];
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      p->M[3 * i + j] = B[3 * i] * B[3 * j] + B[3 * i + 1] * B[3 * j + 1] + B[3 * i + 2] * B[3 * j + 2];
+  p->kfrac.assign(kfrac, kfrac + 3 * nk);
+  p->npw.assign(npw, npw + nk);
+  for (int ax = 0; ax < 3; ++ax) {
+    p->nmax[ax] = nmax[ax];
+    p->h[ax] = 2 * nmax[ax];
+  }
+  p->kernel = kernel_type;
+  p->mu = mu;
+  p->prec = precision;
+  p->cap = workspace_cap ? workspace_cap : kDefaultCap;
+  p->kt = kernel_table(p->N);
+
+  // twiddles exp(-2 pi i e / N), evaluated in long double on the host
+  std::vector<double2> t64(p->N);
+  std::vector<float2> t32(p->N);
+  for (int e = 0; e < p->N; ++e) {
+    const long double ang = -2.0L * 3.141592653589793238462643383279502884L * e / p->N;
+    t64[e] = make_double2((double)cosl(ang), (double)sinl(ang));
+    t32[e] = make_float2((float)t64[e].x, (float)t64[e].y);
+  }
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_miller, sizeof(int) * 3 * (size_t)nk * npw_max);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_npw, sizeof(int) * nk);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_tw64, sizeof(double2) * p->N);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_tw32, sizeof(float2) * p->N);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_err, sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->d_miller, miller, sizeof(int) * 3 * (size_t)nk * npw_max, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_npw, npw, sizeof(int) * nk, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_tw64, t64.data(), sizeof(double2) * p->N, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_tw32, t32.data(), sizeof(float2) * p->N, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    xx_destroy(p);
+    return cuda_status(e);
+  }
+  *out = p;
+  return XX_OK;
+}
+
+int xx_destroy(xx_plan p) {
+  if (!p) return XX_OK;
+  cudaDeviceSynchronize();
+  DevBuf* bufs[] = {&p->u_tgt, &p->u_occ, &p->inter, &p->acc, &p->vt, &p->dvt, &p->box,
+                    &p->stage, &p->dots, &p->partial, &p->dmu_acc, &p->vx_tmp};
+  for (DevBuf* b : bufs) release(*b);
+  if (p->d_miller) cudaFree(p->d_miller);
+  if (p->d_npw) cudaFree(p->d_npw);
+  if (p->d_tw32) cudaFree(p->d_tw32);
+  if (p->d_tw64) cudaFree(p->d_tw64);
+  if (p->d_err) cudaFree(p->d_err);
+  delete p;
+  return XX_OK;
+}
+
+int xx_apply_range(xx_plan p, int k_first, int k_count, const void* c_occ, int ld_occ,
+                   const double* w_occ, int n_occ, const void* c_tgt, int n_tgt, void* vx_out,
+                   void* stream) {
+  if (!p || n_occ < 0 || n_tgt < 0 || k_first < 0 || k_count < 0 || k_first + k_count > p->nk)
+    return XX_ERR_INVALID_ARGUMENT;
+  if (ld_occ == 0) ld_occ = n_occ;
+  if (ld_occ < n_occ) return XX_ERR_INVALID_ARGUMENT;
+  if (n_tgt == 0 || k_count == 0) return XX_OK;
+  if (bad_ptr(c_tgt) || bad_ptr(vx_out) || vx_out == c_tgt || vx_out == c_occ) return XX_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_occ == 0) {
+    const cudaError_t e = cudaMemsetAsync(vx_out, 0, (size_t)k_count * n_tgt * p->npw_max * 16, s);
+    return cuda_status(e);
+  }
+  if (bad_ptr(c_occ) || bad_ptr(w_occ)) return XX_ERR_INVALID_ARGUMENT;
+  return run_apply(p, k_first, k_count, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, vx_out, s);
+}
+
+int xx_apply(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, int n_occ,
+             const void* c_tgt, int n_tgt, void* vx_out, void* stream) {
+  if (!p) return XX_ERR_INVALID_ARGUMENT;
+  return xx_apply_range(p, 0, p->nk, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, vx_out, stream);
+}
+
+int xx_energy_from_vx_range(xx_plan p, int k_first, int k_count, const void* c_tgt,
+                            const double* w_tgt, int n_tgt, const void* vx, double* ex_out,
+                            void* stream) {
+  if (!p || n_tgt < 0 || bad_ptr(ex_out) || k_first < 0 || k_count < 0 || k_first + k_count > p->nk)
+    return XX_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_tgt == 0 || k_count == 0) return cuda_status(cudaMemsetAsync(ex_out, 0, 2 * sizeof(double), s));
+  if (bad_ptr(c_tgt) || bad_ptr(w_tgt) || bad_ptr(vx)) return XX_ERR_INVALID_ARGUMENT;
+  return run_energy_reduce(p, k_first, k_count, c_tgt, w_tgt, n_tgt, vx, ex_out, s);
+}
+
+int xx_energy_from_vx(xx_plan p, const void* c_tgt, const double* w_tgt, int n_tgt, const void* vx,
+                      double* ex_out, void* stream) {
+  if (!p) return XX_ERR_INVALID_ARGUMENT;
+  return xx_energy_from_vx_range(p, 0, p->nk, c_tgt, w_tgt, n_tgt, vx, ex_out, stream);
+}
+
+int xx_energy_range(xx_plan p, int k_first, int k_count, const void* c_occ, int ld_occ,
+                    const double* w_occ, int n_occ, const void* c_tgt, const double* w_tgt,
+                    int n_tgt, void* vx_out, double* ex_out, void* stream) {
+  if (!p || bad_ptr(ex_out)) return XX_ERR_INVALID_ARGUMENT;
+  if (n_tgt > 0 && k_count > 0 && bad_ptr(vx_out)) return XX_ERR_INVALID_ARGUMENT;
+  int st = xx_apply_range(p, k_first, k_count, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, vx_out,
+                          stream);
+  if (st) return st;
+  return xx_energy_from_vx_range(p, k_first, k_count, c_tgt, w_tgt, n_tgt, vx_out, ex_out, stream);
+}
+
+int xx_energy(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, int n_occ,
+              const void* c_tgt, const double* w_tgt, int n_tgt, void* vx_out, double* ex_out,
+              void* stream) {
+  if (!p) return XX_ERR_INVALID_ARGUMENT;
+  return xx_energy_range(p, 0, p->nk, c_occ, ld_occ, w_occ, n_occ, c_tgt, w_tgt, n_tgt, vx_out,
+                         ex_out, stream);
+}
+
+int xx_apply_backward(xx_plan p, const void* c, const double* w, int n_b, const void* vx,
+                      double grad_ex, void* dc_out, double* dmu_out, void* stream) {
+  if (!p || n_b < 0 || !std::isfinite(grad_ex)) return XX_ERR_INVALID_ARGUMENT;
+  if (dmu_out && p->kernel != XX_KERNEL_HSE) return XX_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_b == 0) {
+    if (dmu_out) return cuda_status(cudaMemsetAsync(dmu_out, 0, sizeof(double), s));
+    return XX_OK;
+  }
+  if (bad_ptr(c) || bad_ptr(w)) return XX_ERR_INVALID_ARGUMENT;
+  int st;
+  if (dc_out) {
+    if (dc_out == c) return XX_ERR_INVALID_ARGUMENT;
+    const void* v = vx;
+    if (!v) {
+      if ((st = ensure(p, p->vx_tmp, (size_t)p->nk * n_b * p->npw_max * 16))) return st;
+      if ((st = run_apply(p, 0, p->nk, c, n_b, w, n_b, c, n_b, p->vx_tmp.p, s))) return st;
+      v = p->vx_tmp.p;
+    }
+    const long long rows = (long long)p->nk * n_b;
+    const int blocks = (int)((rows * p->npw_max + 255) / 256);
+    k_scale_rows<<<blocks < 65535 ? blocks : 65535, 256, 0, s>>>(
+        (const double2*)v, w, rows, p->npw_max, grad_ex * kSpin / p->nk, (double2*)dc_out);
+    if ((st = launched(p, 1))) return st;
+  }
+  if (dmu_out) return run_dmu(p, c, w, n_b, grad_ex, dmu_out, s);
+  return XX_OK;
+}
+
+int xx_sync(xx_plan p, void* stream, double timeout_s) {
+  if (!p) return XX_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (timeout_s > 0.0) {
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return XX_ERR_CUDA;
+    cudaEventRecord(ev, s);
+    struct timespec ts0, ts1;
+    clock_gettime(CLOCK_MONOTONIC, &ts0);
+    for (;;) {
+      const cudaError_t q = cudaEventQuery(ev);
+      if (q == cudaSuccess) break;
+      if (q != cudaErrorNotReady) {
+        cudaEventDestroy(ev);
+        return cuda_status(q);
+      }
+      clock_gettime(CLOCK_MONOTONIC, &ts1);
+      const double el = (ts1.tv_sec - ts0.tv_sec) + 1e-9 * (ts1.tv_nsec - ts0.tv_nsec);
+      if (el > timeout_s) {
+        cudaEventDestroy(ev);
+        return XX_ERR_TIMEOUT;
+      }
+      struct timespec nap = {0, 200000};
+      nanosleep(&nap, nullptr);
+    }
+    cudaEventDestroy(ev);
+  } else {
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  int flag = 0;
+  if (cudaMemcpy(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return XX_ERR_CUDA;
+  if (flag) {
+    cudaMemset(p->d_err, 0, sizeof(int));
+    return XX_ERR_DEVICE_FLAG;
+  }
+  return XX_OK;
+}
+
+int xx_set_batch(xx_plan p, int targets_per_batch, int occupied_per_batch) {
+  if (!p || targets_per_batch < 0 || occupied_per_batch < 0) return XX_ERR_INVALID_ARGUMENT;
+  p->ta_user = targets_per_batch;
+  p->tj_user = occupied_per_batch;
+  return XX_OK;
+}
+
+int xx_plan_info(xx_plan p, xx_info* info) {
+  if (!p || !info) return XX_ERR_INVALID_ARGUMENT;
+  std::memset(info, 0, sizeof(*info));
+  for (int i = 0; i < 3; ++i) {
+    info->grid[i] = p->grid[i];
+    info->n_max[i] = p->nmax[i];
+    info->pruned[i] = 2 * p->h[i] + 1;
+  }
+  info->nk = p->nk;
+  info->npw_max = p->npw_max;
+  info->precision = p->prec;
+  info->targets_per_batch = p->ta_last;
+  info->occupied_per_batch = p->tj_last;
+  info->omega = p->omega;
+  info->workspace_bytes = p->ws_bytes;
+  info->peak_workspace_bytes = p->peak_bytes;
+  info->kernel_launches = p->launches;
+  return XX_OK;
+}
+
+}  // extern "C"

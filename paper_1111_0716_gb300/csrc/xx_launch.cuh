@@ -1,0 +1,93 @@
+// xx_launch.cuh -- host launchers of the templated kernels and the per-grid-
+// length kernel table.  Each supported FFT length N is instantiated in its own
+// translation unit (xx_n<N>.cu) so that the builds run in parallel.
+#pragma once
+
+#include "xx_kernels.cuh"
+
+namespace xx {
+
+constexpr int kThreads = 256;
+
+struct KernelSet {
+  void (*pass_a)(const PairArgs&, cudaStream_t);
+  void (*pass_b)(const PairArgs&, cudaStream_t);
+  void (*pass_b_dmu)(const PairArgs&, cudaStream_t);
+  void (*pass_c)(const PairArgs&, cudaStream_t);
+  void (*s2g_z)(const GridArgs&, cudaStream_t);
+  void (*s2g_xy)(const GridArgs&, cudaStream_t);
+};
+
+struct KernelTable {
+  int n;
+  KernelSet f32, f64;
+  void (*g2s_xy)(const GridArgs&, cudaStream_t);
+  void (*g2s_z)(const GridArgs&, cudaStream_t);
+};
+
+// Returns the table for FFT length n, or nullptr when n is not built in.
+const KernelTable* kernel_table(int n);
+
+template <typename K> inline void allow_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int N, typename T> void launch_pass_a(const PairArgs& p, cudaStream_t s) {
+  const size_t sm = smem_plane<N, T>();
+  allow_smem(k_pass_a<N, kThreads, T>, sm);
+  k_pass_a<N, kThreads, T><<<dim3(p.TA, N), kThreads, sm, s>>>(p);
+}
+template <int N, typename T> void launch_pass_b(const PairArgs& p, cudaStream_t s) {
+  const size_t sm = smem_pencil<N, T>(p.P1, p.P3);
+  allow_smem(k_pass_b<N, kThreads, T>, sm);
+  k_pass_b<N, kThreads, T><<<dim3(p.P2, p.TA * p.TJ), kThreads, sm, s>>>(p);
+}
+template <int N, typename T> void launch_pass_b_dmu(const PairArgs& p, cudaStream_t s) {
+  const size_t sm = smem_pencil<N, T>(p.P1, 0);
+  allow_smem(k_pass_b_dmu<N, kThreads, T>, sm);
+  k_pass_b_dmu<N, kThreads, T><<<dim3(p.P2, p.TA * p.TJ), kThreads, sm, s>>>(p);
+}
+template <int N, typename T> void launch_pass_c(const PairArgs& p, cudaStream_t s) {
+  const size_t sm = smem_plane<N, T>();
+  allow_smem(k_pass_c<N, kThreads, T>, sm);
+  k_pass_c<N, kThreads, T><<<dim3(p.TA, N), kThreads, sm, s>>>(p);
+}
+template <int N, typename T> void launch_s2g_z(const GridArgs& g, cudaStream_t s) {
+  const size_t sm = smem_pencil<N, T>(g.Q1, 0);
+  allow_smem(k_s2g_z<N, kThreads, T>, sm);
+  k_s2g_z<N, kThreads, T><<<dim3(g.Q2, g.nb), kThreads, sm, s>>>(g);
+}
+template <int N, typename T> void launch_s2g_xy(const GridArgs& g, cudaStream_t s) {
+  const size_t sm = smem_plane<N, T>();
+  allow_smem(k_s2g_xy<N, kThreads, T>, sm);
+  k_s2g_xy<N, kThreads, T><<<dim3(g.nb, N), kThreads, sm, s>>>(g);
+}
+template <int N> void launch_g2s_xy(const GridArgs& g, cudaStream_t s) {
+  const size_t sm = smem_plane<N, double>();
+  allow_smem(k_g2s_xy<N, kThreads>, sm);
+  k_g2s_xy<N, kThreads><<<dim3(g.nb, N), kThreads, sm, s>>>(g);
+}
+template <int N> void launch_g2s_z(const GridArgs& g, cudaStream_t s) {
+  const size_t sm = smem_pencil<N, double>(g.Q1, 0);
+  allow_smem(k_g2s_z<N, kThreads>, sm);
+  k_g2s_z<N, kThreads><<<dim3(g.Q2, g.nb), kThreads, sm, s>>>(g);
+}
+
+template <int N> const KernelTable* make_table() {
+  static const KernelTable t = {
+      N,
+      {launch_pass_a<N, float>, launch_pass_b<N, float>, launch_pass_b_dmu<N, float>,
+       launch_pass_c<N, float>, launch_s2g_z<N, float>, launch_s2g_xy<N, float>},
+      {launch_pass_a<N, double>, launch_pass_b<N, double>, launch_pass_b_dmu<N, double>,
+       launch_pass_c<N, double>, launch_s2g_z<N, double>, launch_s2g_xy<N, double>},
+      launch_g2s_xy<N>,
+      launch_g2s_z<N>};
+  return &t;
+}
+
+}  // namespace xx
+
+#define XX_INSTANTIATE(N) \
+  namespace xx {          \
+  const KernelTable* kernel_table_##N() { return make_table<N>(); } \
+  }

@@ -1,0 +1,351 @@
+"""Python binding of libxx (ctypes): argument marshalling only.
+
+Every step of the exchange computation runs in the CUDA library; this module
+passes device pointers (torch tensors' ``data_ptr()``), sizes and the current
+CUDA stream to the C entry points of ``include/xx.h`` under the same names.
+There is no CPU fallback: if libxx.so is missing or no GPU is present, the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libxx.so")
+
+XX_OK = 0
+XX_FP32_MIXED = 0
+XX_FP64 = 1
+XX_KERNEL_HSE = 0
+XX_KERNEL_COULOMB_G0_DROPPED = 1
+SPIN = 2.0
+
+STATUS = {
+    0: "XX_OK", -1: "XX_ERR_INVALID_ARGUMENT", -2: "XX_ERR_UNSUPPORTED_GRID",
+    -3: "XX_ERR_GRID_ALIASING", -4: "XX_ERR_OUT_OF_MEMORY", -5: "XX_ERR_CUDA",
+    -6: "XX_ERR_DEVICE_FLAG", -7: "XX_ERR_TIMEOUT", -8: "XX_ERR_NO_DEVICE",
+}
+
+# every symbol declared in include/xx.h
+EXPORTS = ("xx_create", "xx_destroy", "xx_apply", "xx_apply_range", "xx_energy",
+           "xx_energy_range", "xx_energy_from_vx", "xx_energy_from_vx_range",
+           "xx_apply_backward", "xx_sync", "xx_set_batch", "xx_plan_info", "xx_status_string")
+
+
+class XXError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s failed: %s (%s)" % (where, STATUS.get(status, status),
+                                                  xx_status_string(status)))
+
+
+class xx_info(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int * 3), ("n_max", ctypes.c_int * 3),
+                ("pruned", ctypes.c_int * 3), ("nk", ctypes.c_int), ("npw_max", ctypes.c_int),
+                ("precision", ctypes.c_int), ("targets_per_batch", ctypes.c_int),
+                ("occupied_per_batch", ctypes.c_int), ("omega", ctypes.c_double),
+                ("workspace_bytes", ctypes.c_size_t), ("peak_workspace_bytes", ctypes.c_size_t),
+                ("kernel_launches", ctypes.c_longlong)]
+
+
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load libxx.so (built in-tree by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libxx.so not built (%s): run __graft_entry__.build() first" % p)
+    lib = ctypes.CDLL(p)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    lib.xx_create.argtypes = [ctypes.POINTER(P), P, P, I, P, P, I, P, I, D, I, S]
+    lib.xx_destroy.argtypes = [P]
+    lib.xx_apply.argtypes = [P, P, I, P, I, P, I, P, P]
+    lib.xx_apply_range.argtypes = [P, I, I, P, I, P, I, P, I, P, P]
+    lib.xx_energy.argtypes = [P, P, I, P, I, P, P, I, P, P, P]
+    lib.xx_energy_range.argtypes = [P, I, I, P, I, P, I, P, P, I, P, P, P]
+    lib.xx_energy_from_vx.argtypes = [P, P, P, I, P, P, P]
+    lib.xx_energy_from_vx_range.argtypes = [P, I, I, P, P, I, P, P, P]
+    lib.xx_apply_backward.argtypes = [P, P, P, I, P, D, P, P, P]
+    lib.xx_sync.argtypes = [P, P, D]
+    lib.xx_set_batch.argtypes = [P, I, I]
+    lib.xx_plan_info.argtypes = [P, ctypes.POINTER(xx_info)]
+    lib.xx_status_string.argtypes = [I]
+    lib.xx_status_string.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("xx_status_string",):
+            getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != XX_OK:
+        raise XXError(status, where)
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------- C entry points --
+
+def xx_status_string(status: int) -> str:
+    return load().xx_status_string(int(status)).decode()
+
+
+def xx_create(lattice, grid, kfrac, npw, miller, kernel_type, mu, precision, workspace_cap=0):
+    """Host arrays in, plan handle (c_void_p) out."""
+    lat = np.ascontiguousarray(lattice, dtype=np.float64).reshape(9)
+    g = np.ascontiguousarray(grid, dtype=np.int32).reshape(3)
+    kf = np.ascontiguousarray(kfrac, dtype=np.float64).reshape(-1, 3)
+    nk = kf.shape[0]
+    npw_a = np.ascontiguousarray(npw, dtype=np.int32).reshape(nk)
+    mil = np.ascontiguousarray(miller, dtype=np.int32).reshape(nk, -1, 3)
+    plan = ctypes.c_void_p()
+    _check(load().xx_create(ctypes.byref(plan), _np_ptr(lat), _np_ptr(g), nk, _np_ptr(kf),
+                            _np_ptr(npw_a), mil.shape[1], _np_ptr(mil), int(kernel_type),
+                            float(mu), int(precision), int(workspace_cap)), "xx_create")
+    return plan
+
+
+def xx_destroy(plan):
+    _check(load().xx_destroy(plan), "xx_destroy")
+
+
+def xx_apply(plan, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, vx_out, stream=None):
+    _check(load().xx_apply(plan, _dptr(c_occ), int(ld_occ), _dptr(w_occ), int(n_occ),
+                           _dptr(c_tgt), int(n_tgt), _dptr(vx_out), _stream_ptr(stream)),
+           "xx_apply")
+
+
+def xx_apply_range(plan, k_first, k_count, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, vx_out,
+                   stream=None):
+    _check(load().xx_apply_range(plan, int(k_first), int(k_count), _dptr(c_occ), int(ld_occ),
+                                 _dptr(w_occ), int(n_occ), _dptr(c_tgt), int(n_tgt),
+                                 _dptr(vx_out), _stream_ptr(stream)), "xx_apply_range")
+
+
+def xx_energy_range(plan, k_first, k_count, c_occ, ld_occ, w_occ, n_occ, c_tgt, w_tgt, n_tgt,
+                    vx_out, ex_out, stream=None):
+    _check(load().xx_energy_range(plan, int(k_first), int(k_count), _dptr(c_occ), int(ld_occ),
+                                  _dptr(w_occ), int(n_occ), _dptr(c_tgt), _dptr(w_tgt),
+                                  int(n_tgt), _dptr(vx_out), _dptr(ex_out), _stream_ptr(stream)),
+           "xx_energy_range")
+
+
+def xx_energy_from_vx_range(plan, k_first, k_count, c_tgt, w_tgt, n_tgt, vx, ex_out, stream=None):
+    _check(load().xx_energy_from_vx_range(plan, int(k_first), int(k_count), _dptr(c_tgt),
+                                          _dptr(w_tgt), int(n_tgt), _dptr(vx), _dptr(ex_out),
+                                          _stream_ptr(stream)), "xx_energy_from_vx_range")
+
+
+def xx_energy(plan, c_occ, ld_occ, w_occ, n_occ, c_tgt, w_tgt, n_tgt, vx_out, ex_out, stream=None):
+    _check(load().xx_energy(plan, _dptr(c_occ), int(ld_occ), _dptr(w_occ), int(n_occ),
+                            _dptr(c_tgt), _dptr(w_tgt), int(n_tgt), _dptr(vx_out), _dptr(ex_out),
+                            _stream_ptr(stream)), "xx_energy")
+
+
+def xx_energy_from_vx(plan, c_tgt, w_tgt, n_tgt, vx, ex_out, stream=None):
+    _check(load().xx_energy_from_vx(plan, _dptr(c_tgt), _dptr(w_tgt), int(n_tgt), _dptr(vx),
+                                    _dptr(ex_out), _stream_ptr(stream)), "xx_energy_from_vx")
+
+
+def xx_apply_backward(plan, c, w, n_b, vx, grad_ex, dc_out, dmu_out, stream=None):
+    _check(load().xx_apply_backward(plan, _dptr(c), _dptr(w), int(n_b), _dptr(vx),
+                                    float(grad_ex), _dptr(dc_out), _dptr(dmu_out),
+                                    _stream_ptr(stream)), "xx_apply_backward")
+
+
+def xx_sync(plan, stream=None, timeout_s: float = 0.0):
+    _check(load().xx_sync(plan, _stream_ptr(stream), float(timeout_s)), "xx_sync")
+
+
+def xx_set_batch(plan, targets_per_batch: int, occupied_per_batch: int):
+    _check(load().xx_set_batch(plan, int(targets_per_batch), int(occupied_per_batch)),
+           "xx_set_batch")
+
+
+def xx_plan_info(plan) -> dict:
+    info = xx_info()
+    _check(load().xx_plan_info(plan, ctypes.byref(info)), "xx_plan_info")
+    return {f: (list(getattr(info, f)) if isinstance(getattr(info, f), ctypes.Array)
+                else getattr(info, f)) for f, _ in xx_info._fields_}
+
+
+# ------------------------------------------------------------ high level --
+
+class Plan:
+    """Owns an xx_plan for one cell / grid / k-mesh / basis (and kernel, precision)."""
+
+    def __init__(self, lattice, grid, kfrac, npw, miller, kernel=XX_KERNEL_HSE, mu=0.106,
+                 precision=XX_FP32_MIXED, workspace_cap=0):
+        self.handle = xx_create(lattice, grid, kfrac, npw, miller, kernel, mu, precision,
+                                workspace_cap)
+        self.nk = int(np.asarray(kfrac).reshape(-1, 3).shape[0])
+        self.npw_max = int(np.asarray(miller).reshape(self.nk, -1, 3).shape[1])
+        self.kernel = kernel
+        self.mu = float(mu)
+        self.precision = precision
+
+    @classmethod
+    def from_workload(cls, wl, precision=XX_FP32_MIXED, mu=None, workspace_cap=0):
+        return cls(wl.lattice, wl.grid, wl.kfrac, wl.npw, wl.miller, kernel=wl.kernel,
+                   mu=wl.mu if mu is None else mu, precision=precision,
+                   workspace_cap=workspace_cap)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            xx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        return xx_plan_info(self.handle)
+
+    def set_batch(self, targets: int, occupied: int):
+        xx_set_batch(self.handle, targets, occupied)
+
+    def apply(self, c_occ, w_occ, c_tgt, vx_out=None, stream=None):
+        """V_x c_tgt.  c_* complex128 CUDA tensors [nk][nb][npw_max]; w_occ float64 [nk][n_occ]."""
+        import torch
+        n_occ = c_occ.shape[1]
+        n_tgt = c_tgt.shape[1]
+        if vx_out is None:
+            vx_out = torch.empty_like(c_tgt)
+        xx_apply(self.handle, c_occ, n_occ, w_occ, n_occ, c_tgt, n_tgt, vx_out, stream)
+        return vx_out
+
+    def apply_shared(self, c, w_occ, n_occ, vx_out=None, stream=None):
+        """V_x c for all bands of c, occupied set = the first n_occ bands of c (grids shared)."""
+        import torch
+        n_tgt = c.shape[1]
+        if vx_out is None:
+            vx_out = torch.empty_like(c)
+        xx_apply(self.handle, c, n_tgt, w_occ, n_occ, c, n_tgt, vx_out, stream)
+        return vx_out
+
+    def apply_range(self, k_first, k_count, c_occ, w_occ, c_tgt, vx_out=None, stream=None):
+        """V_x c_tgt for target k-points k_first..k_first+k_count-1 (c_tgt holds only those)."""
+        import torch
+        n_occ = c_occ.shape[1]
+        if vx_out is None:
+            vx_out = torch.empty_like(c_tgt)
+        xx_apply_range(self.handle, k_first, k_count, c_occ, n_occ, w_occ, n_occ, c_tgt,
+                       c_tgt.shape[1], vx_out, stream)
+        return vx_out
+
+    def energy_range(self, k_first, k_count, c_occ, w_occ, c_tgt, w_tgt, vx_out=None,
+                     ex_out=None, stream=None):
+        import torch
+        if vx_out is None:
+            vx_out = torch.empty_like(c_tgt)
+        if ex_out is None:
+            ex_out = torch.empty(2, dtype=torch.float64, device=c_tgt.device)
+        n_occ = c_occ.shape[1]
+        xx_energy_range(self.handle, k_first, k_count, c_occ, n_occ, w_occ, n_occ, c_tgt, w_tgt,
+                        c_tgt.shape[1], vx_out, ex_out, stream)
+        return ex_out, vx_out
+
+    def energy(self, c_occ, w_occ, c_tgt, w_tgt, vx_out=None, ex_out=None, stream=None,
+               shared=False):
+        """(E_x as a device float64[2] (Re, Im), V_x c_tgt)."""
+        import torch
+        n_tgt = c_tgt.shape[1]
+        n_occ = w_occ.shape[1]
+        if vx_out is None:
+            vx_out = torch.empty_like(c_tgt)
+        if ex_out is None:
+            ex_out = torch.empty(2, dtype=torch.float64, device=c_tgt.device)
+        ld = n_tgt if shared else n_occ
+        xx_energy(self.handle, c_tgt if shared else c_occ, ld, w_occ, n_occ, c_tgt, w_tgt, n_tgt,
+                  vx_out, ex_out, stream)
+        return ex_out, vx_out
+
+    def backward(self, c, w, grad_ex=1.0, vx=None, want_dc=True, want_dmu=True, stream=None):
+        import torch
+        n_b = c.shape[1]
+        dc = torch.empty_like(c) if want_dc else None
+        dmu = torch.empty(1, dtype=torch.float64, device=c.device) if want_dmu else None
+        xx_apply_backward(self.handle, c, w, n_b, vx, grad_ex, dc, dmu, stream)
+        return dc, dmu
+
+    def sync(self, timeout_s: float = 0.0, stream=None):
+        xx_sync(self.handle, stream, timeout_s)
+
+
+def _exchange_function():
+    import torch
+
+    class ExchangeEnergy(torch.autograd.Function):
+        """E_x[c] with c both occupied and target (the usual self-consistent case).
+
+        forward(c, w, mu, plan) -> E_x (float64 scalar).  ``mu`` is a float64
+        tensor equal to the plan's screening parameter; its gradient is
+        dE_x/dmu.  The complex gradient follows torch's convention
+        (2 dL/dc*): 2 grad (s w / N_k) V_x c.  The backward reuses V_x c saved by
+        the forward and recomputes codensities for dE_x/dmu (no pair grids are
+        stored).
+        """
+
+        @staticmethod
+        def forward(ctx, c, w, mu, plan):
+            c = c.contiguous()
+            w = w.contiguous()
+            ex, vx = plan.energy(c, w, c, w, shared=True)
+            ctx.plan = plan
+            ctx.save_for_backward(c, w, vx)
+            return ex[0]
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            c, w, vx = ctx.saved_tensors
+            plan = ctx.plan
+            g = float(grad_out.item())
+            want_dc = ctx.needs_input_grad[0]
+            want_dmu = ctx.needs_input_grad[2] and plan.kernel == XX_KERNEL_HSE
+            dc, dmu = plan.backward(c, w, grad_ex=g, vx=vx, want_dc=want_dc, want_dmu=want_dmu)
+            gc = 2.0 * dc if dc is not None else None
+            gmu = dmu.reshape(()) if dmu is not None else None
+            return gc, None, gmu, None
+
+    return ExchangeEnergy
+
+
+_EXF = None
+
+
+def exchange_energy(c, w, mu, plan):
+    """Differentiable E_x[c] (see ExchangeEnergy)."""
+    global _EXF
+    if _EXF is None:
+        _EXF = _exchange_function()
+    return _EXF.apply(c, w, mu, plan)

@@ -1,0 +1,111 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+symbol include/xx.h declares, and rejects bad arguments before any GPU work."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1111_0716_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1111_0716_gb300 import xx
+    return xx
+
+
+def declared_symbols():
+    with open(os.path.join(ROOT, "include", "xx.h")) as f:
+        src = f.read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(xx_\w+)\s*\(", src, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ("xx_create", "xx_destroy", "xx_apply", "xx_energy", "xx_apply_backward",
+              "xx_sync", "xx_status_string"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(xx_\w+)", out))
+    for n in declared_symbols():
+        assert n in exported, n
+        assert hasattr(lib.load(), n)
+    assert set(lib.EXPORTS) == set(declared_symbols())
+
+
+def test_status_strings(lib):
+    for code in range(-8, 1):
+        s = lib.xx_status_string(code)
+        assert isinstance(s, str) and s and s != "unknown status"
+    assert lib.xx_status_string(-99) == "unknown status"
+
+
+def _create(lib, wl, grid=None, kernel=None, mu=None, prec=0):
+    return lib.xx_create(wl.lattice, wl.grid if grid is None else grid, wl.kfrac, wl.npw,
+                         wl.miller, wl.kernel if kernel is None else kernel,
+                         wl.mu if mu is None else mu, prec)
+
+
+def _status(fn):
+    from paper_1111_0716_gb300 import xx
+    try:
+        fn()
+    except xx.XXError as e:
+        return e.status
+    return 0
+
+
+def test_rejects_bad_arguments_before_gpu_work(lib):
+    wl = synth.tiny_cubic()
+    assert _status(lambda: _create(lib, wl, grid=(25, 25, 25))) == -2        # unsupported length
+    assert _status(lambda: _create(lib, wl, grid=(24, 24, 48))) == -2        # unequal axes
+    assert _status(lambda: _create(lib, wl, kernel=7)) == -1
+    assert _status(lambda: _create(lib, wl, mu=0.0)) == -1                   # screened needs mu > 0
+    assert _status(lambda: _create(lib, wl, mu=float("nan"))) == -1
+    assert _status(lambda: _create(lib, wl, prec=3)) == -1
+    bad = wl.replace(npw=np.array([wl.npw_max + 1], dtype=np.int32))
+    assert _status(lambda: _create(lib, bad)) == -1
+    flat = wl.replace(lattice=np.zeros((3, 3)))
+    assert _status(lambda: _create(lib, flat)) == -1
+
+
+def test_rejects_grids_with_codensity_wrap_around(lib):
+    # 48^3 basis (n_max = 9) on a 24^3 grid: 24 < 4*9 + 1
+    wl = synth.sweep_cell(2)
+    assert _status(lambda: _create(lib, wl, grid=(24, 24, 24))) == -3
+    # n_max = 6 on 24: 24 < 25 is rejected, on 32: 32 >= 25 passes the check
+    wl6 = synth.sweep_cell(0)
+    assert int(wl6.n_max().max()) == 6
+    assert _status(lambda: _create(lib, wl6, grid=(24, 24, 24))) == -3
+
+
+def test_null_plan_and_pointers(lib):
+    L = lib.load()
+    assert L.xx_apply(None, None, 0, None, 0, None, 0, None, None) == -1
+    assert L.xx_apply_range(None, 0, 1, None, 0, None, 0, None, 0, None, None) == -1
+    assert L.xx_energy(None, None, 0, None, 0, None, None, 0, None, None, None) == -1
+    assert L.xx_apply_backward(None, None, None, 0, None, 1.0, None, None, None) == -1
+    assert L.xx_sync(None, None, 1.0) == -1
+    assert L.xx_set_batch(None, 1, 1) == -1
+    assert L.xx_plan_info(None, None) == -1
+    assert L.xx_destroy(None) == 0
+    assert L.xx_create(None, None, None, 0, None, None, 0, None, 0, 0.0, 0, 0) == -1
+
+
+def test_no_device_is_reported_without_a_gpu(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    wl = synth.tiny_cubic()
+    assert _status(lambda: _create(lib, wl)) == -8

@@ -1,0 +1,184 @@
+"""CUDA path vs the FP64 CPU oracle, element by element, through the C ABI.
+
+Tolerances: mixed precision max|dV_x c| <= 1e-5 max|V_x c| and |dE_x| <= 1e-5
+|E_x| (the two precision settings of the method agree to 1e-3 %); all-FP64
+path 1e-11.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1111_0716_gb300 import synth
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+def rhombo24(kernel=synth.KERNEL_HSE, seed=21):
+    """Rhombohedral cell with a 2x2x2 MP mesh, targets beyond the occupied set."""
+    wl = synth.make_workload("rhombo24", synth.rhombohedral_lattice(7.5, 65.0), (24,) * 3,
+                             synth.monkhorst_pack(2), 2.4, 4, 6, [1.0, 1.0, 0.75, 0.3], seed,
+                             kernel=kernel)
+    assert np.all(4 * wl.n_max() + 1 <= 24)
+    return wl
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    return gu.need_gpu()
+
+
+@pytest.fixture(scope="module")
+def oracle_cache(oracle_mod):
+    cache = {}
+
+    def get(key, fn):
+        if key not in cache:
+            cache[key] = fn()
+        return cache[key]
+    return get
+
+
+@pytest.mark.parametrize("prec,tol", [(0, gu.FP32_TOL), (1, gu.FP64_TOL)])
+def test_tiny_cubic(gpu, oracle_mod, oracle_cache, prec, tol):
+    wl = synth.tiny_cubic()
+    ref = oracle_cache("tiny", lambda: oracle_mod.apply(wl))
+    e_ref, _ = oracle_mod.energy_from_vx(wl, ref)
+    vx, (e, e_im), _ = gu.run(wl, prec)
+    assert gu.rel_max(vx, ref) <= tol
+    assert abs(e - e_ref) <= tol * abs(e_ref)
+    assert abs(e_im) <= tol * abs(e_ref)
+
+
+@pytest.mark.parametrize("kernel", [synth.KERNEL_HSE, synth.KERNEL_COULOMB])
+@pytest.mark.parametrize("prec,tol", [(0, gu.FP32_TOL), (1, gu.FP64_TOL)])
+def test_k_mesh_targets_beyond_occupied(gpu, oracle_mod, oracle_cache, kernel, prec, tol):
+    wl = rhombo24(kernel)
+    ref = oracle_cache(("rh", kernel), lambda: oracle_mod.apply(wl))
+    e_ref, _ = oracle_mod.energy_from_vx(wl, ref)
+    # separate occupied array (no grid sharing)
+    vx, (e, _), _ = gu.run(wl, prec, shared=False)
+    assert gu.rel_max(vx, ref) <= tol
+    assert abs(e - e_ref) <= tol * abs(e_ref)
+    # shared grids: occupied = leading bands of the target array
+    vx2, (e2, _), _ = gu.run(wl, prec, shared=True)
+    assert gu.rel_max(vx2, ref) <= tol
+    assert abs(e2 - e_ref) <= tol * abs(e_ref)
+
+
+def test_ragged_batches_match(gpu, oracle_mod, oracle_cache):
+    wl = rhombo24()
+    base, (e0, _), _ = gu.run(wl, 1)
+    for batch in [(1, 1), (5, 3), (4, 4), (6, 4)]:
+        vx, (e, _), info = gu.run(wl, 1, batch=batch)
+        assert info["targets_per_batch"] == batch[0] and info["occupied_per_batch"] == batch[1]
+        assert gu.rel_max(vx, base) <= 1e-13
+        assert abs(e - e0) <= 1e-13 * abs(e0)
+
+
+def test_deterministic(gpu):
+    wl = rhombo24()
+    a, ea, _ = gu.run(wl, 0)
+    b, eb, _ = gu.run(wl, 0)
+    assert np.array_equal(a, b) and ea == eb
+
+
+def test_edge_cases(gpu, oracle_mod):
+    torch, xx = gpu
+    wl = rhombo24()
+    plan = xx.Plan.from_workload(wl, precision=1)
+    ct = gu.dev(wl.c_tgt)
+    # no occupied bands: V_x c = 0
+    vx = torch.full_like(ct, 7.0)
+    xx.xx_apply(plan.handle, ct, 0, gu.dev(wl.w_occ), 0, ct, ct.shape[1], vx)
+    assert float(vx.abs().max()) == 0.0
+    # no targets: nothing to do
+    xx.xx_apply(plan.handle, ct, 0, gu.dev(wl.w_occ), 4, ct, 0, vx)
+    # zero-weight occupied bands contribute nothing
+    w0 = wl.w_occ.copy()
+    w0[:, 2:] = 0.0
+    ref = oracle_mod.apply(wl, c_occ=wl.c_occ[:, :2], w_occ=w0[:, :2])
+    vx1, _, _ = gu.run(wl, 1, shared=False, w_occ=w0)
+    assert gu.rel_max(vx1, ref) <= gu.FP64_TOL
+    # a single target band and a single occupied band
+    ref1 = oracle_mod.apply(wl, c_occ=wl.c_occ[:, :1], w_occ=wl.w_occ[:, :1], c_tgt=wl.c_tgt[:, :1])
+    vx2, _, _ = gu.run(wl, 1, shared=False, c_occ=wl.c_occ[:, :1], w_occ=wl.w_occ[:, :1],
+                       c_tgt=wl.c_tgt[:, :1], w_tgt=wl.w_tgt[:, :1])
+    assert gu.rel_max(vx2, ref1) <= gu.FP64_TOL
+    plan.close()
+
+
+def test_k_range_shards_sum_to_full(gpu, oracle_mod):
+    """Disjoint target k-ranges (the multi-GPU decomposition) reproduce the full result."""
+    torch, xx = gpu
+    wl = rhombo24()
+    full, (e_full, _), _ = gu.run(wl, 1, shared=False)
+    plan = xx.Plan.from_workload(wl, precision=1)
+    co, wo = gu.dev(wl.c_occ), gu.dev(wl.w_occ)
+    parts, e_sum = [], 0.0
+    for k0, kn in [(0, 3), (3, 1), (4, 4)]:
+        ct = gu.dev(wl.c_tgt[k0:k0 + kn])
+        wt = gu.dev(wl.w_tgt[k0:k0 + kn])
+        ex, vx = plan.energy_range(k0, kn, co, wo, ct, wt)
+        parts.append(vx.cpu().numpy())
+        e_sum += float(ex[0].item())
+    plan.close()
+    assert gu.rel_max(np.concatenate(parts), full) <= 1e-13
+    assert abs(e_sum - e_full) <= 1e-13 * abs(e_full)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, gu.FP32_TOL), (1, gu.FP64_TOL)])
+def test_differentiation_cell_48(gpu, oracle_mod, oracle_cache, prec, tol):
+    wl = synth.differentiation_cell()
+    ref = oracle_cache("cfg4", lambda: oracle_mod.apply(wl))
+    e_ref, _ = oracle_mod.energy_from_vx(wl, ref)
+    vx, (e, _), _ = gu.run(wl, prec)
+    assert gu.rel_max(vx, ref) <= tol
+    assert abs(e - e_ref) <= tol * abs(e_ref)
+
+
+@pytest.mark.parametrize("shell", synth.PW_SHELLS)
+def test_plane_wave_cells_exact_lattice_sum(gpu, shell):
+    """Single-plane-wave orbitals: V_x c_a = lam_a c_a with the exact lattice sum."""
+    from tests.test_oracle_pins import pw_closed_form
+    wl = synth.plane_wave_cell(shell)
+    lam, ex = pw_closed_form(wl)
+    ref = lam[:, None] * wl.c_tgt[0]
+    vx, (e, _), _ = gu.run(wl, 0)
+    assert gu.rel_max(vx[0], ref) <= gu.FP32_TOL
+    assert abs(e - ex) <= gu.FP32_TOL * abs(ex)
+    # Dirac exchange of the homogeneous gas after the q -> 0 correction
+    omega = abs(np.linalg.det(wl.lattice))
+    n_e = 2 * wl.npw[0]
+    kf = (3 * math.pi ** 2 * n_e / omega) ** (1 / 3)
+    qc = (6 * math.pi ** 2 / omega) ** (1 / 3)
+    corr = -wl.npw[0] * 16 * math.pi ** 2 * qc / (2 * math.pi) ** 3
+    assert abs((e + corr) / n_e / (-3 * kf / (4 * math.pi)) - 1) <= 0.03
+    if shell <= 5:
+        vx64, (e64, _), _ = gu.run(wl, 1)
+        assert gu.rel_max(vx64[0], ref) <= gu.FP64_TOL
+        assert abs(e64 - ex) <= gu.FP64_TOL * abs(ex)
+
+
+@pytest.mark.parametrize("i", range(len(synth.SWEEP_GRIDS)))
+@pytest.mark.parametrize("kernel", [synth.KERNEL_HSE, synth.KERNEL_COULOMB])
+def test_precision_sweep_cells(gpu, oracle_mod, i, kernel):
+    """Uneven sweep: each cell in mixed precision, sampled targets vs the oracle,
+    Hermiticity on every target, and an FP64 slice."""
+    wl = synth.sweep_cell(i, kernel)
+    vx, (e, e_im), _ = gu.run(wl, 0)
+    sel = [(0, 0), (0, wl.n_tgt - 1)]
+    ref = oracle_mod.apply(wl, sel=sel)
+    got = np.stack([vx[k, a] for k, a in sel])
+    assert gu.rel_max(got, ref) <= gu.FP32_TOL
+    assert gu.hermitian_defect(wl.c_tgt, vx) <= gu.FP32_TOL
+    # per-target energy contributions of the sampled targets
+    for (k, a), r in zip(sel, ref):
+        d_gpu = np.vdot(wl.c_tgt[k, a], vx[k, a]).real
+        d_ref = np.vdot(wl.c_tgt[k, a], r).real
+        assert abs(d_gpu - d_ref) <= gu.FP32_TOL * abs(d_ref)
+    # FP64 on two target bands, all occupied bands
+    vx64, _, _ = gu.run(wl, 1, shared=False, c_tgt=wl.c_tgt[:, [0, wl.n_tgt - 1]],
+                        w_tgt=wl.w_tgt[:, [0, wl.n_tgt - 1]])
+    assert gu.rel_max(vx64[0], ref) <= gu.FP64_TOL
