@@ -1,0 +1,361 @@
+"""Benchmark of the GB300 Fock-exchange path: band-pair applications per second.
+
+One step = one full pass of the exchange path over the beta-boron-sized
+workload (96^3 grid, Gamma-centred 2x2x2 mesh, 160 occupied / 192 target
+bands: 1,966,080 band pairs): sphere->grid of every orbital, the three fused
+band-pair passes for every (k, q, target batch, occupied batch), grid->sphere
+of V_x c and the E_x reduction, all through the C ABI (xx_energy).
+
+Printed as one JSON line (rank 0):
+  value      band pairs / s with inputs resident in HBM (CUDA events, K steps)
+  e2e        the same through the public API with pinned host buffers: H2D of
+             the orbitals and occupations, xx_energy, D2H of V_x c and E_x
+  roofline   the dominant kernel's algorithmic bytes per launch over its mean
+             launch duration (events on its stream during the timed steps),
+             against the measured HBM copy bandwidth
+  cpu_baseline  the FP64 CPU oracle, as it stands, on a bounded sample
+  fp64_slice    the all-FP64 GPU path on a slice of the same workload
+  --impl reference  times the oracle as the reference arm.
+Multi-GPU (torchrun): each rank runs an independent workload (its own seed),
+weak scaling; value = all ranks' pairs / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "band-pair exchange applications/s and % HBM roofline, FP32-mixed vs FP64 GPU"
+UNIT = "band-pair applications/s"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        self.index = index
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for i, n in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def pass_bytes_per_step(wl, TA, TJ, elem=8):
+    """Algorithmic HBM bytes of each band-pair pass over one step.
+
+    Per band pair each pass streams one grid of N^3 complex values in and one
+    out (16 B per grid point in FP32 complex): pass A reads u_j and writes the
+    codensity transform, pass B reads and writes it, pass C reads it and u_j.
+    Per-target terms are paid once per (target, occupied batch): pass A reads
+    u_a, pass C reads u_a's accumulator and writes it back in FP64 (32 B/pt).
+    """
+    n3 = wl.grid[0] ** 3
+    pairs = wl.pair_count()
+    n_jb = -(-wl.n_occ // TJ)            # occupied batches per (k, q, target)
+    per_target = wl.nk * wl.n_tgt * wl.nk * n_jb
+    return {
+        "pass_a": 2 * elem * n3 * pairs + elem * n3 * per_target,
+        "pass_b": 2 * elem * n3 * pairs,
+        "pass_c": 2 * elem * n3 * pairs + 32 * n3 * per_target,
+    }
+
+
+def run_oracle_sample(wl, n_occ_sample):
+    """The FP64 oracle on target (k=0, a=0), all q, the first n_occ_sample occupied bands."""
+    from oracle import oracle
+    t0 = time.perf_counter()
+    oracle.apply(wl, sel=[(0, 0)], c_occ=wl.c_occ[:, :n_occ_sample],
+                 w_occ=wl.w_occ[:, :n_occ_sample])
+    dt = time.perf_counter() - t0
+    pairs = wl.nk * n_occ_sample
+    return pairs / dt, dt, pairs, oracle.num_threads()
+
+
+def reference_arm(args, rank, world):
+    """The oracle timed as the reference arm (rank 0 only)."""
+    if rank != 0:
+        return
+    from paper_1111_0716_gb300 import synth
+    wl = synth.beta_boron()
+    n_s = args.oracle_occ
+    for _ in range(args.warmup):
+        run_oracle_sample(wl, max(1, n_s // 4))
+    rates, total = [], 0.0
+    for _ in range(args.steps):
+        r, dt, pairs, cores = run_oracle_sample(wl, n_s)
+        rates.append(r)
+        total += dt
+    value = float(np.sum([args.steps * wl.nk * n_s])) / total
+    sample = ("target (k=0, a=0) x 8 q x %d occupied bands = %d pairs of the 96^3 beta-boron "
+              "workload per step" % (n_s, wl.nk * n_s))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "grid": 96, "nk": wl.nk, "n_occ": wl.n_occ,
+                       "n_tgt": wl.n_tgt, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--oracle-occ", type=int, default=8,
+                    help="occupied bands in the oracle sample (pairs = 8 x this)")
+    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 slice")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1111_0716_gb300 import synth, xx
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = synth.beta_boron(seed=3 + rank)
+    pairs = wl.pair_count()
+    plan = xx.Plan.from_workload(wl, precision=xx.XX_FP32_MIXED)
+    stream = torch.cuda.current_stream()
+    c = torch.from_numpy(wl.c_tgt).cuda()
+    w = torch.from_numpy(wl.w_tgt).cuda()
+    vx = torch.empty_like(c)
+    ex = torch.empty(2, dtype=torch.float64, device="cuda")
+
+    def step():
+        xx.xx_energy(plan.handle, c, c.shape[1], w, wl.n_occ, c, w, c.shape[1], vx, ex)
+
+    # w as the occupied weights: the first n_occ columns of each k row (ld = n_tgt)
+    w_occ = torch.from_numpy(wl.w_occ).cuda()
+
+    def step():  # noqa: F811
+        xx.xx_energy(plan.handle, c, c.shape[1], w_occ, wl.n_occ, c, w, c.shape[1], vx, ex)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.profile(True)
+    plan.profile_read(reset=True)
+    launches0 = plan.info()["kernel_launches"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    t = e0.elapsed_time(e1) / 1e3
+    launches = plan.info()["kernel_launches"] - launches0
+    prof = plan.profile_read(reset=True)
+    plan.profile(False)
+    info = plan.info()
+    e_x = float(ex[0].item())
+    if world > 1:
+        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    value = world * pairs * args.steps / t
+
+    # end to end through the public API with pinned host buffers
+    c_h = torch.from_numpy(wl.c_tgt).pin_memory()
+    w_h = torch.from_numpy(wl.w_tgt).pin_memory()
+    wo_h = torch.from_numpy(wl.w_occ).pin_memory()
+    vx_h = torch.empty(vx.shape, dtype=vx.dtype).pin_memory()
+    ex_h = torch.empty(2, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        c.copy_(c_h, non_blocking=True)
+        w.copy_(w_h, non_blocking=True)
+        w_occ.copy_(wo_h, non_blocking=True)
+        xx.xx_energy(plan.handle, c, c.shape[1], w_occ, wl.n_occ, c, w, c.shape[1], vx, ex)
+        vx_h.copy_(vx, non_blocking=True)
+        ex_h.copy_(ex, non_blocking=True)
+
+    e2e_steps = max(1, min(args.steps, 2))
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = f0.elapsed_time(f1) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    h2d = c.numel() * 16 + (w.numel() + w_occ.numel()) * 8
+    d2h = vx.numel() * 16 + 16
+
+    # roofline of the dominant kernel: algorithmic bytes over its event-timed
+    # device time during the timed steps, against the measured HBM copy rate
+    hbm, peak_kind = peaks()
+    TA, TJ = info["targets_per_batch"], info["occupied_per_batch"]
+    model = pass_bytes_per_step(wl, TA, TJ)
+    dom = max(("pass_a", "pass_b", "pass_c"), key=lambda k: prof[k][0])
+    ms_tot, n_l = prof[dom]
+    mean_s = ms_tot / 1e3 / max(n_l, 1)
+    bytes_per_launch = model[dom] * args.steps / max(n_l, 1)
+    achieved = bytes_per_launch / mean_s / 1e9 if mean_s > 0 else 0.0
+    path_bytes = sum(model.values()) * args.steps
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+                "bytes_per_launch": bytes_per_launch, "mean_launch_ms": mean_s * 1e3,
+                "launches": n_l,
+                "path": {"achieved": path_bytes / t / 1e9 / world * world, "frac":
+                         path_bytes / t / 1e9 / hbm, "bytes_per_pair_per_point": 48}}
+    shares = {k: v[0] for k, v in prof.items() if v[1]}
+    tot = sum(shares.values()) or 1.0
+    kernel_share = {k: round(v / tot, 4) for k, v in shares.items()}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name + " (beta-boron-sized rhombohedral cell)", "grid": 96,
+                       "nk": wl.nk, "n_occ": wl.n_occ, "n_tgt": wl.n_tgt,
+                       "pairs_per_step": pairs, "precision": "FP32 FFTs and products, FP64 "
+                       "accumulation, kernel table and reductions",
+                       "batch": [TA, TJ], "l2": "inputs larger than L2 (orbital grids %.1f GB)"
+                       % (wl.nk * wl.n_tgt * 96 ** 3 * 8 / 1e9), "E_x": e_x},
+            "e2e": {"value": world * pairs * e2e_steps / t_e2e, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "roofline": roofline, "kernel_time_share": kernel_share,
+            "peak_workspace_gb": info["peak_workspace_bytes"] / 1e9}
+    if clk:
+        line["clocks"] = clk
+
+    if rank == 0 and not args.no_fp64:
+        # all-FP64 GPU path on a slice: target k=0, 4 target bands, 16 occupied, all q
+        p64 = xx.Plan.from_workload(wl, precision=xx.XX_FP64)
+        nt, no = 4, 16
+        ct = torch.from_numpy(wl.c_tgt[:1, :nt].copy()).cuda()
+        co = torch.from_numpy(wl.c_occ[:, :no].copy()).cuda()
+        wo = torch.from_numpy(wl.w_occ[:, :no].copy()).cuda()
+        v64 = torch.empty_like(ct)
+        p64.apply_range(0, 1, co, wo, ct, v64)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        p64.apply_range(0, 1, co, wo, ct, v64)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        t64 = g0.elapsed_time(g1) / 1e3
+        p_slice = nt * wl.nk * no
+        # same slice in mixed precision for the like-for-like ratio
+        p32 = xx.Plan.from_workload(wl, precision=xx.XX_FP32_MIXED)
+        v32 = torch.empty_like(ct)
+        p32.apply_range(0, 1, co, wo, ct, v32)
+        torch.cuda.synchronize()
+        g0.record(stream)
+        p32.apply_range(0, 1, co, wo, ct, v32)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        t32 = g0.elapsed_time(g1) / 1e3
+        line["fp64_slice"] = {"value": p_slice / t64, "unit": UNIT,
+                              "fp32_mixed_same_slice": p_slice / t32,
+                              "sample": "target k=0, %d target x %d occupied bands x 8 q = %d pairs"
+                              % (nt, no, p_slice)}
+        p64.close()
+        p32.close()
+
+    if rank == 0 and world == 1 and not args.no_baseline:
+        r, dt, p_s, cores = run_oracle_sample(wl, args.oracle_occ)
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "target (k=0, a=0) x 8 q x %d occupied = %d pairs, %.1f s"
+                                % (args.oracle_occ, p_s, dt)}
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -192,6 +192,27 @@ int xx_sync(xx_plan plan, void *stream, double timeout_s);
  * the automatic choice.  Takes effect at the next call. */
 int xx_set_batch(xx_plan plan, int targets_per_batch, int occupied_per_batch);
 
+/* Kernel classes of the per-kernel timing (xx_profile_read). */
+#define XX_PROF_PASS_A 0          /* codensity + forward xy FFT */
+#define XX_PROF_PASS_B 1          /* z FFT, kernel multiply, inverse z FFT */
+#define XX_PROF_PASS_C 2          /* inverse xy FFT, multiply by u_j, accumulate */
+#define XX_PROF_SPHERE_TO_GRID 3  /* scatter + inverse 3D FFT of orbitals */
+#define XX_PROF_GRID_TO_SPHERE 4  /* forward 3D FFT + gather of V_x u */
+#define XX_PROF_KERNEL_TABLE 5    /* v(k - q + G) table */
+#define XX_PROF_REDUCE 6          /* E_x reduction */
+#define XX_PROF_PASS_B_DMU 7      /* forward z FFT x dv/dmu reduction */
+#define XX_PROF_CLASSES 8
+
+/* Turn per-kernel-class timing on or off: when on, every launch group of the
+ * plan is bracketed by CUDA events on its stream (measurement use; adds two
+ * event records per group). */
+int xx_profile_enable(xx_plan plan, int enable);
+
+/* Device time in ms and number of timed launch groups per kernel class since
+ * the last reset, for classes 0 .. n_classes-1 (host arrays).  Waits for the
+ * recorded events.  reset != 0 discards the records. */
+int xx_profile_read(xx_plan plan, double *ms, long long *launches, int n_classes, int reset);
+
 /* Fill *info with the plan's facts. */
 int xx_plan_info(xx_plan plan, xx_info *info);
 

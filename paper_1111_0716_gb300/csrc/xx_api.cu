@@ -203,6 +203,12 @@ struct xx_plan_s {
   DevBuf u_tgt, u_occ, inter, acc, vt, dvt, box, stage, dots, partial, dmu_acc, vx_tmp;
   size_t ws_bytes = 0, peak_bytes = 0;
   long long launches = 0;
+  // optional per-kernel-class timing with events on the launch stream
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Rec { int cls; int e0, e1; };
+  std::vector<Rec> recs;
+  size_t ev_next = 0;
 };
 
 namespace {
@@ -259,6 +265,32 @@ int launched(xx_plan p, int count) {
   return cuda_status(cudaGetLastError());
 }
 
+// Profiling brackets: record an event before and after the launches of one
+// kernel class on stream s (no-ops unless profiling is enabled).
+int prof_event(xx_plan p) {
+  if (p->ev_next == p->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    p->ev_pool.push_back(e);
+  }
+  return (int)p->ev_next++;
+}
+
+int prof_begin(xx_plan p, cudaStream_t s) {
+  if (!p->profiling) return -1;
+  const int e = prof_event(p);
+  if (e >= 0) cudaEventRecord(p->ev_pool[e], s);
+  return e;
+}
+
+void prof_end(xx_plan p, int cls, int e0, cudaStream_t s) {
+  if (!p->profiling || e0 < 0) return;
+  const int e1 = prof_event(p);
+  if (e1 < 0) return;
+  cudaEventRecord(p->ev_pool[e1], s);
+  p->recs.push_back({cls, e0, e1});
+}
+
 // sphere -> grid for nb orbitals of k-point k: c[b][npw_max] -> u[b][N^3]
 int sphere_to_grid(xx_plan p, int k, const double2* c, int nb, void* u, cudaStream_t s) {
   const size_t eb = elem_bytes(p);
@@ -288,6 +320,7 @@ int sphere_to_grid(xx_plan p, int k, const double2* c, int nb, void* u, cudaStre
     g.Q3 = Q3;
     g.scale = 1.0 / std::sqrt(p->omega);
     g.err = p->d_err;
+    const int e = prof_begin(p, s);
     cudaMemsetAsync(p->box.p, 0, (size_t)cb * Q1 * Q2 * Q3 * eb, s);
     const int blocks = (int)(((long long)cb * g.npw + 255) / 256);
     if (p->prec == XX_FP64)
@@ -296,6 +329,7 @@ int sphere_to_grid(xx_plan p, int k, const double2* c, int nb, void* u, cudaStre
       k_s2g_scatter<float><<<blocks, 256, 0, s>>>(g);
     kset(p).s2g_z(g, s);
     kset(p).s2g_xy(g, s);
+    prof_end(p, XX_PROF_SPHERE_TO_GRID, e, s);
     if ((st = launched(p, 3))) return st;
   }
   return XX_OK;
@@ -329,10 +363,12 @@ int grid_to_sphere(xx_plan p, int k, const double2* f, int nb, double2* out, cud
     g.Q3 = Q3;
     g.scale = std::sqrt(p->omega) / (double)n3(p);
     g.err = p->d_err;
+    const int e = prof_begin(p, s);
     p->kt->g2s_xy(g, s);
     p->kt->g2s_z(g, s);
     const int blocks = (int)(((long long)cb * p->npw_max + 255) / 256);
     k_g2s_gather<<<blocks, 256, 0, s>>>(g);
+    prof_end(p, XX_PROF_GRID_TO_SPHERE, e, s);
     if ((st = launched(p, 3))) return st;
   }
   return XX_OK;
@@ -358,10 +394,12 @@ int kernel_table_for(xx_plan p, int k, int q, bool with_dmu, cudaStream_t s) {
   a.inv_n = 1.0 / (double)n3(p);
   a.inv_n2 = a.inv_n * a.inv_n;
   const int blocks = (int)((nbox + 255) / 256);
+  const int e = prof_begin(p, s);
   if (p->prec == XX_FP64)
     k_vtab<double><<<blocks, 256, 0, s>>>((double*)p->vt.p, with_dmu ? (double*)p->dvt.p : nullptr, a);
   else
     k_vtab<float><<<blocks, 256, 0, s>>>((float*)p->vt.p, with_dmu ? (float*)p->dvt.p : nullptr, a);
+  prof_end(p, XX_PROF_KERNEL_TABLE, e, s);
   return launched(p, 1);
 }
 
@@ -456,9 +494,15 @@ int run_apply(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, const do
           a.u_occ = grid_ptr(p, shared, q, j0, n_occ, n_tgt);
           a.acc = (double2*)p->acc.p + (long long)a0 * n3(p);
           a.w_occ = w_occ + (long long)q * n_occ + j0;
+          int e = prof_begin(p, s);
           ks.pass_a(a, s);
+          prof_end(p, XX_PROF_PASS_A, e, s);
+          e = prof_begin(p, s);
           ks.pass_b(a, s);
+          prof_end(p, XX_PROF_PASS_B, e, s);
+          e = prof_begin(p, s);
           ks.pass_c(a, s);
+          prof_end(p, XX_PROF_PASS_C, e, s);
           if ((st = launched(p, 3))) return st;
         }
       }
@@ -475,9 +519,11 @@ int run_energy_reduce(xx_plan p, int k0, int kn, const void* c_tgt, const double
   const int rows = kn * n_tgt;
   int st = ensure(p, p->dots, (size_t)rows * 16);
   if (st) return st;
+  const int e = prof_begin(p, s);
   k_dot_rows<<<rows, kRedThreads, 0, s>>>((const double2*)c_tgt, (const double2*)vx, p->d_npw + k0,
                                            n_tgt, p->npw_max, (double2*)p->dots.p);
   k_energy<<<1, kRedThreads, 0, s>>>((const double2*)p->dots.p, w_tgt, rows, 0.5 * kSpin / p->nk, ex_out);
+  prof_end(p, XX_PROF_REDUCE, e, s);
   return launched(p, 2);
 }
 
@@ -504,8 +550,12 @@ int run_dmu(xx_plan p, const void* c, const double* w, int n_b, double grad, dou
           PairArgs a = pair_args(p, ta, tj);
           a.u_tgt = grid_ptr(p, true, k, a0, n_b, n_b);
           a.u_occ = grid_ptr(p, true, q, j0, n_b, n_b);
+          int e = prof_begin(p, s);
           ks.pass_a(a, s);
+          prof_end(p, XX_PROF_PASS_A, e, s);
+          e = prof_begin(p, s);
           ks.pass_b_dmu(a, s);
+          prof_end(p, XX_PROF_PASS_B_DMU, e, s);
           k_dmu_batch<<<1, kRedThreads, 0, s>>>((const double*)p->partial.p, P(p, 1), ta, tj,
                                                 w + (long long)k * n_b + a0,
                                                 w + (long long)q * n_b + j0, (double*)p->dmu_acc.p);
@@ -657,6 +707,7 @@ int xx_destroy(xx_plan p) {
   if (p->d_tw32) cudaFree(p->d_tw32);
   if (p->d_tw64) cudaFree(p->d_tw64);
   if (p->d_err) cudaFree(p->d_err);
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   delete p;
   return XX_OK;
 }
@@ -793,6 +844,35 @@ int xx_set_batch(xx_plan p, int targets_per_batch, int occupied_per_batch) {
   if (!p || targets_per_batch < 0 || occupied_per_batch < 0) return XX_ERR_INVALID_ARGUMENT;
   p->ta_user = targets_per_batch;
   p->tj_user = occupied_per_batch;
+  return XX_OK;
+}
+
+int xx_profile_enable(xx_plan p, int enable) {
+  if (!p) return XX_ERR_INVALID_ARGUMENT;
+  p->profiling = enable != 0;
+  return XX_OK;
+}
+
+int xx_profile_read(xx_plan p, double* ms, long long* launches, int n_classes, int reset) {
+  if (!p || n_classes < 0 || (n_classes > 0 && (!ms || !launches))) return XX_ERR_INVALID_ARGUMENT;
+  for (int c = 0; c < n_classes; ++c) {
+    ms[c] = 0.0;
+    launches[c] = 0;
+  }
+  for (const auto& r : p->recs) {
+    float t = 0.0f;
+    cudaError_t e = cudaEventSynchronize(p->ev_pool[r.e1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, p->ev_pool[r.e0], p->ev_pool[r.e1]);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (r.cls < n_classes) {
+      ms[r.cls] += t;
+      launches[r.cls] += 1;
+    }
+  }
+  if (reset) {
+    p->recs.clear();
+    p->ev_next = 0;
+  }
   return XX_OK;
 }
 

@@ -403,7 +403,9 @@ __global__ void __launch_bounds__(NT) k_pass_c(PairArgs p) {
   for (int i = 0; i < IPT; ++i) {
     const int it = threadIdx.x + i * NT;
     if (it < N * A) {
-      const int k1 = it % A, y = it / A;
+      // same slot -> (y, x) map as plane_inverse's last step
+      const int k1 = it % A, row = it / A;
+      const int y = row / B + A * (row % B);
 #pragma unroll
       for (int k2 = 0; k2 < B; ++k2) {
         double2* o = dst + y * N + k1 + A * k2;

@@ -33,7 +33,11 @@ STATUS = {
 # every symbol declared in include/xx.h
 EXPORTS = ("xx_create", "xx_destroy", "xx_apply", "xx_apply_range", "xx_energy",
            "xx_energy_range", "xx_energy_from_vx", "xx_energy_from_vx_range",
-           "xx_apply_backward", "xx_sync", "xx_set_batch", "xx_plan_info", "xx_status_string")
+           "xx_apply_backward", "xx_sync", "xx_set_batch", "xx_profile_enable",
+           "xx_profile_read", "xx_plan_info", "xx_status_string")
+
+PROF_CLASSES = ("pass_a", "pass_b", "pass_c", "sphere_to_grid", "grid_to_sphere",
+                "kernel_table", "reduce", "pass_b_dmu")
 
 
 class XXError(RuntimeError):
@@ -77,6 +81,8 @@ def load(path: Optional[str] = None):
     lib.xx_sync.argtypes = [P, P, D]
     lib.xx_set_batch.argtypes = [P, I, I]
     lib.xx_plan_info.argtypes = [P, ctypes.POINTER(xx_info)]
+    lib.xx_profile_enable.argtypes = [P, I]
+    lib.xx_profile_read.argtypes = [P, P, P, I, I]
     lib.xx_status_string.argtypes = [I]
     lib.xx_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -189,6 +195,20 @@ def xx_set_batch(plan, targets_per_batch: int, occupied_per_batch: int):
            "xx_set_batch")
 
 
+def xx_profile_enable(plan, enable: bool):
+    _check(load().xx_profile_enable(plan, 1 if enable else 0), "xx_profile_enable")
+
+
+def xx_profile_read(plan, reset: bool = True) -> dict:
+    """{class: (ms, launch groups)} of the per-kernel-class event timing."""
+    n = len(PROF_CLASSES)
+    ms = np.zeros(n, dtype=np.float64)
+    cnt = np.zeros(n, dtype=np.int64)
+    _check(load().xx_profile_read(plan, _np_ptr(ms), _np_ptr(cnt), n, 1 if reset else 0),
+           "xx_profile_read")
+    return {c: (float(ms[i]), int(cnt[i])) for i, c in enumerate(PROF_CLASSES)}
+
+
 def xx_plan_info(plan) -> dict:
     info = xx_info()
     _check(load().xx_plan_info(plan, ctypes.byref(info)), "xx_plan_info")
@@ -230,6 +250,12 @@ class Plan:
 
     def info(self) -> dict:
         return xx_plan_info(self.handle)
+
+    def profile(self, enable: bool = True):
+        xx_profile_enable(self.handle, enable)
+
+    def profile_read(self, reset: bool = True) -> dict:
+        return xx_profile_read(self.handle, reset)
 
     def set_batch(self, targets: int, occupied: int):
         xx_set_batch(self.handle, targets, occupied)
