@@ -1,0 +1,62 @@
+"""Full-size workloads in the launch configuration the benchmark times.
+
+The CUDA path runs the whole operator; the oracle computes sampled targets one
+by one (each target needs every occupied band of every q); properties that
+hold at any size (Hermiticity of <c_b|V_x c_a> at every k) cover the rest; an
+FP64 GPU slice checks the all-FP64 path at the same size.
+"""
+import numpy as np
+import pytest
+
+from paper_1111_0716_gb300 import synth
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    return gu.need_gpu()
+
+
+def fp64_target_slice(xx, wl, k, a):
+    plan = xx.Plan.from_workload(wl, precision=1)
+    co, wo = gu.dev(wl.c_occ), gu.dev(wl.w_occ)
+    ct = gu.dev(wl.c_tgt[k:k + 1, a:a + 1])
+    vx = plan.apply_range(k, 1, co, wo, ct)
+    plan.sync(timeout_s=600.0)
+    out = vx.cpu().numpy()[0, 0]
+    plan.close()
+    return out
+
+
+def test_alpha_boron_48_mp444(gpu, oracle_mod):
+    torch, xx = gpu
+    wl = synth.alpha_boron()
+    vx, (e, e_im), info = gu.run(wl, 0)
+    assert abs(e_im) <= gu.FP32_TOL * abs(e)
+    assert gu.hermitian_defect(wl.c_tgt, vx) <= gu.FP32_TOL
+    sel = [(0, 0), (wl.nk - 1, wl.n_tgt - 1)]
+    ref = oracle_mod.apply(wl, sel=sel)
+    got = np.stack([vx[k, a] for k, a in sel])
+    assert gu.rel_max(got, ref) <= gu.FP32_TOL
+    v64 = fp64_target_slice(xx, wl, *sel[1])
+    assert gu.rel_max(v64, ref[1]) <= gu.FP64_TOL
+
+
+@pytest.mark.slow
+def test_beta_boron_96_gamma222(gpu, oracle_mod):
+    torch, xx = gpu
+    wl = synth.beta_boron()
+    vx, (e, e_im), info = gu.run(wl, 0)
+    assert abs(e_im) <= gu.FP32_TOL * abs(e)
+    assert gu.hermitian_defect(wl.c_tgt, vx) <= gu.FP32_TOL
+    # a target at a zone-boundary k-point in the fractionally occupied range
+    k, a = wl.nk - 1, 155
+    ref = oracle_mod.apply(wl, sel=[(k, a)])[0]
+    assert gu.rel_max(vx[k, a], ref) <= gu.FP32_TOL
+    d_gpu = np.vdot(wl.c_tgt[k, a], vx[k, a]).real
+    d_ref = np.vdot(wl.c_tgt[k, a], ref).real
+    assert abs(d_gpu - d_ref) <= gu.FP32_TOL * abs(d_ref)
+    v64 = fp64_target_slice(xx, wl, k, a)
+    assert gu.rel_max(v64, ref) <= gu.FP64_TOL
