@@ -67,6 +67,7 @@ extern "C" {
 #define XX_ERR_DEVICE_FLAG (-6)
 #define XX_ERR_TIMEOUT (-7)
 #define XX_ERR_NO_DEVICE (-8)
+#define XX_ERR_SIZE_LIMIT (-9)
 
 #define XX_FP32_MIXED 0   /* FFTs and pointwise products in FP32, sums in FP64 */
 #define XX_FP64 1         /* every step in FP64 */
@@ -215,6 +216,31 @@ int xx_profile_read(xx_plan plan, double *ms, long long *launches, int n_classes
 
 /* Fill *info with the plan's facts. */
 int xx_plan_info(xx_plan plan, xx_info *info);
+
+/*
+ * E_x reduction for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this entry point exists for callers whose device memory is
+ * already reserved by their own memory manager (a framework's caching
+ * allocator, a fixed per-process budget), or that must not hit the
+ * device-wide synchronisation cudaFree implies.  It computes the same
+ * fixed-order FP64 reduction as xx_energy_from_vx, needs no plan, and calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   nk, n_tgt, npw_max: sizes of c_tgt and vx ([nk][n_tgt][npw_max] complex128,
+ *       device); npw: device int [nk] basis sizes; w_tgt: device double
+ *       [nk][n_tgt]; ex_out: device double[2] = {Re E_x, Im E_x}.
+ * Its per-target partial sums live in one fixed device array of
+ * XX_NOALLOC_MAX_ROWS complex128 entries (256 KiB) that every GPU loading the
+ * library holds until the process exits; nk * n_tgt above that limit returns
+ * XX_ERR_SIZE_LIMIT.  The first call on a device looks up the array's device
+ * address (with that device current), so make that first call before any
+ * stream capture.  All calls on a device share the array: calls whose work
+ * overlaps on the GPU (different streams, concurrent threads) race and must be
+ * serialised by the caller.  Every entry is written before it is read, so no
+ * clearing is needed between calls.
+ */
+#define XX_NOALLOC_MAX_ROWS 16384
+int xx_energy_from_vx_noalloc(int nk, int n_tgt, int npw_max, const int *npw, const void *c_tgt,
+                              const double *w_tgt, const void *vx, double *ex_out, void *stream);
 
 /* Static description of a status code. */
 const char *xx_status_string(int status);

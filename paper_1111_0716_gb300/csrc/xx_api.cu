@@ -587,6 +587,7 @@ const char* xx_status_string(int status) {
     case XX_ERR_DEVICE_FLAG: return "device-side check failed (inconsistent basis data)";
     case XX_ERR_TIMEOUT: return "timed out waiting for the stream";
     case XX_ERR_NO_DEVICE: return "no usable CUDA device";
+    case XX_ERR_SIZE_LIMIT: return "size exceeds the fixed scratch of the no-allocation entry point (XX_NOALLOC_MAX_ROWS)";
     default: return "unknown status";
   }
 }

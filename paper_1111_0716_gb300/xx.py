@@ -28,13 +28,15 @@ STATUS = {
     0: "XX_OK", -1: "XX_ERR_INVALID_ARGUMENT", -2: "XX_ERR_UNSUPPORTED_GRID",
     -3: "XX_ERR_GRID_ALIASING", -4: "XX_ERR_OUT_OF_MEMORY", -5: "XX_ERR_CUDA",
     -6: "XX_ERR_DEVICE_FLAG", -7: "XX_ERR_TIMEOUT", -8: "XX_ERR_NO_DEVICE",
+    -9: "XX_ERR_SIZE_LIMIT",
 }
+XX_NOALLOC_MAX_ROWS = 16384
 
 # every symbol declared in include/xx.h
 EXPORTS = ("xx_create", "xx_destroy", "xx_apply", "xx_apply_range", "xx_energy",
            "xx_energy_range", "xx_energy_from_vx", "xx_energy_from_vx_range",
            "xx_apply_backward", "xx_sync", "xx_set_batch", "xx_profile_enable",
-           "xx_profile_read", "xx_plan_info", "xx_status_string")
+           "xx_profile_read", "xx_plan_info", "xx_status_string", "xx_energy_from_vx_noalloc")
 
 PROF_CLASSES = ("pass_a", "pass_b", "pass_c", "sphere_to_grid", "grid_to_sphere",
                 "kernel_table", "reduce", "pass_b_dmu")
@@ -83,6 +85,7 @@ def load(path: Optional[str] = None):
     lib.xx_plan_info.argtypes = [P, ctypes.POINTER(xx_info)]
     lib.xx_profile_enable.argtypes = [P, I]
     lib.xx_profile_read.argtypes = [P, P, P, I, I]
+    lib.xx_energy_from_vx_noalloc.argtypes = [I, I, I, P, P, P, P, P, P]
     lib.xx_status_string.argtypes = [I]
     lib.xx_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -173,6 +176,13 @@ def xx_energy(plan, c_occ, ld_occ, w_occ, n_occ, c_tgt, w_tgt, n_tgt, vx_out, ex
     _check(load().xx_energy(plan, _dptr(c_occ), int(ld_occ), _dptr(w_occ), int(n_occ),
                             _dptr(c_tgt), _dptr(w_tgt), int(n_tgt), _dptr(vx_out), _dptr(ex_out),
                             _stream_ptr(stream)), "xx_energy")
+
+
+def xx_energy_from_vx_noalloc(nk, n_tgt, npw_max, npw, c_tgt, w_tgt, vx, ex_out, stream=None):
+    """E_x reduction without a plan or any device allocation (fixed device scratch)."""
+    _check(load().xx_energy_from_vx_noalloc(int(nk), int(n_tgt), int(npw_max), _dptr(npw),
+                                            _dptr(c_tgt), _dptr(w_tgt), _dptr(vx), _dptr(ex_out),
+                                            _stream_ptr(stream)), "xx_energy_from_vx_noalloc")
 
 
 def xx_energy_from_vx(plan, c_tgt, w_tgt, n_tgt, vx, ex_out, stream=None):
