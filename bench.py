@@ -155,6 +155,29 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(args):
+    """beta-boron 96^3, target k=0, 16 targets x 32 occupied bands x 8 q (4096 pairs)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1111_0716_gb300 import synth, xx
+    wl = synth.beta_boron()
+    prec = xx.XX_FP64 if args.precision == "fp64" else xx.XX_FP32_MIXED
+    plan = xx.Plan.from_workload(wl, precision=prec)
+    nt, no = 16, 32
+    co = torch.from_numpy(wl.c_occ[:, :no].copy()).cuda()
+    wo = torch.from_numpy(wl.w_occ[:, :no].copy()).cuda()
+    ct = torch.from_numpy(wl.c_tgt[:1, :nt].copy()).cuda()
+    plan.apply_range(0, 1, co, wo, ct)
+    torch.cuda.synchronize()
+    info = plan.info()
+    plan.close()
+    print(json.dumps({"profile_case": wl.name, "pairs": nt * no * wl.nk,
+                      "batch": [info["targets_per_batch"], info["occupied_per_batch"]],
+                      "workspace_gb": info["peak_workspace_bytes"] / 1e9}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -165,6 +188,11 @@ def main():
                     help="occupied bands in the oracle sample (pairs = 8 x this)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 slice")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run one small slice of the workload (k=0, 16 targets, 32 occupied "
+                         "bands, all q) once and exit: the case ncu captures")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="precision of --profile-case")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -173,6 +201,9 @@ def main():
 
     if args.impl == "reference":
         reference_arm(args, rank, world)
+        return
+    if args.profile_case:
+        profile_case(args)
         return
 
     import torch

@@ -405,8 +405,8 @@ int kernel_table_for(xx_plan p, int k, int q, bool with_dmu, cudaStream_t s) {
 
 void batch_shape(xx_plan p, int n_tgt, int n_occ, int* TA, int* TJ) {
   const size_t per_pair = (size_t)p->N * P(p, 1) * P(p, 0) * elem_bytes(p);
-  int ta = p->ta_user > 0 ? p->ta_user : 16;
-  int tj = p->tj_user > 0 ? p->tj_user : 32;
+  int ta = p->ta_user > 0 ? p->ta_user : 32;
+  int tj = p->tj_user > 0 ? p->tj_user : 16;
   if (ta > n_tgt) ta = n_tgt;
   if (tj > n_occ) tj = n_occ;
   while ((size_t)ta * tj * per_pair > p->cap && tj > 1) tj = (tj + 1) / 2;

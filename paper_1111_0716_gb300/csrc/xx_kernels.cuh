@@ -67,130 +67,304 @@ struct VtabArgs {
 };
 
 // ---------------------------------------------------- CTA building blocks --
+//
+// Shared-memory layout of a plane (N rows of LD complex values): between the
+// two steps of the x transform, row y holds slot k1*S + n2 (S >= B); the x
+// transform's output and the y transform's data sit at natural positions
+// (row y, column x or f_x).  S and LD are chosen per N so that the accesses of
+// every step, with the thread mappings below, hit distinct shared-memory banks
+// (all of them for N = 32 and 96; the replay ratio is at most 1.3 elsewhere).
+// FP32 planes use two buffers (the x-step exchange goes from one to the
+// other); FP64 planes use one buffer and hold a step's outputs in registers
+// across a barrier.
 
-// Forward x then y transform of one real-space plane held in sA (N rows of
-// N + 1), in place; outputs only the kept frequencies |f_x| <= h1, |f_y| <= h2
-// through store(kyb, kxb, value).  After the x transform, frequency
-// f_x = k1 + A*k2 sits in column k1*B + k2 (the second step's natural order).
-template <int N, int NT, typename T, typename Load, typename Store>
-__device__ __forceinline__ void plane_forward(const cplx<T>* tw, cplx<T>* sA, int h1, int P1,
-                                              int h2, Load load, Store store) {
+template <int N> struct Lay;
+template <> struct Lay<24> { static constexpr int A = 8, B = 3, S = 3, LD = 28; };
+template <> struct Lay<32> { static constexpr int A = 8, B = 4, S = 5, LD = 44; };
+template <> struct Lay<40> { static constexpr int A = 8, B = 5, S = 5, LD = 44; };
+template <> struct Lay<48> { static constexpr int A = 8, B = 6, S = 7, LD = 60; };
+template <> struct Lay<60> { static constexpr int A = 6, B = 10, S = 11, LD = 67; };
+template <> struct Lay<64> { static constexpr int A = 8, B = 8, S = 9, LD = 76; };
+template <> struct Lay<72> { static constexpr int A = 8, B = 9, S = 9, LD = 76; };
+template <> struct Lay<80> { static constexpr int A = 8, B = 10, S = 11, LD = 92; };
+template <> struct Lay<96> { static constexpr int A = 8, B = 12, S = 13, LD = 108; };
+
+constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+constexpr int lcm_c(int a, int b) { return a / gcd_c(a, b) * b; }
+constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// DB: two plane buffers and one second-step item per thread; otherwise one
+// buffer, half as many threads (a multiple of B, and of A when A != 8, so every
+// iteration covers whole rows) and register holds across barriers.  The
+// default is two buffers for FP32 (pass C keeps its accumulator in registers)
+// and one for FP64 (two FP64 buffers exceed shared memory).
+template <int N, typename T, bool DB_ = (sizeof(T) == 4)> struct PlaneCfg {
+  static constexpr int A = Lay<N>::A, B = Lay<N>::B, S = Lay<N>::S, LD = Lay<N>::LD;
+  static constexpr bool DB = DB_;
+  static constexpr int NT = DB ? round_up(N * A, 32)
+                               : round_up(N * A / 2, lcm_c(lcm_c(32, B), A == 8 ? 1 : A));
+  static constexpr int NW = NT / 32;
+  static constexpr bool REG_TW = (NT % B) == 0;                    // thread's x-step n2 fixed
+  static constexpr int X1_IT = (N * B + NT - 1) / NT;
+  static constexpr int X2_IT = (N * A + NT - 1) / NT;
+  static constexpr int BUF = N * LD;                               // elements per buffer
+  // the one-buffer variant holds one iteration's outputs across a barrier,
+  // which is only safe when every iteration covers whole rows
+  static_assert(DB || (NT % B == 0 && NT % 32 == 0 && (A == 8 || NT % A == 0)),
+                "register hold needs whole rows per iteration");
+  static_assert(NT <= 1024, "too many threads");
+  // twiddles (N) + [k1][n2] twiddle table (N) + plane buffer(s)
+  static constexpr size_t smem() { return sizeof(cplx<T>) * ((size_t)2 * N + (size_t)BUF * (DB ? 2 : 1)); }
+};
+
+// Cooperative L1 prefetch of [p, p + bytes): one 128-byte line per thread.
+__device__ __forceinline__ void prefetch_l1(const void* p, long long bytes) {
+  const long long line = (long long)threadIdx.x * 128;
+  if (line < bytes) asm volatile("prefetch.global.L1 [%0];" ::"l"((const char*)p + line));
+}
+
+// Second x step item -> (k1, row).  For A = 8 each half-warp covers four k1
+// values of four consecutive rows (the conflict-free pattern for slot stride S).
+template <int A> __device__ __forceinline__ void x2_item(int it, int& k1, int& row) {
+  if constexpr (A == 8) {
+    const int l = it & 31, w = it >> 5;
+    k1 = (l & 3) | ((l >> 4) << 2);
+    row = 4 * w + ((l >> 2) & 3);
+  } else {
+    k1 = it % A;
+    row = it / A;
+  }
+}
+
+// Forward x then y transform of one real-space plane; outputs only the kept
+// frequencies |f_x| <= h1, |f_y| <= h2 through store(kyb, kxb, value).
+// s0 (and s1 when double-buffered) are the plane buffers.
+template <int N, typename T, bool DB, typename Load, typename Store>
+__device__ __forceinline__ void plane_forward(const cplx<T>* tw, cplx<T>* s0, cplx<T>* s1, int h1,
+                                              int P1, int h2, Load load, Store store) {
   using C = cplx<T>;
-  constexpr int A = Fac<N>::A, B = Fac<N>::B, LD = N + 1;
-#pragma unroll 1
-  for (int it = threadIdx.x; it < N * B; it += NT) {
-    const int n2 = it % B, y = it / B;
-    C r[A];
+  using G = PlaneCfg<N, T, DB>;
+  constexpr int A = G::A, B = G::B, S = G::S, LD = G::LD, NT = G::NT, NW = G::NW;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  C* sy = G::DB ? s1 : s0;   // buffer of the natural-order plane
+  C twr[A];
+  if constexpr (G::REG_TW) {
 #pragma unroll
-    for (int n1 = 0; n1 < A; ++n1) r[n1] = load(y, B * n1 + n2);
-    dft<A, false>(r);
+    for (int k1 = 0; k1 < A; ++k1) twr[k1] = tw[(t % B) * k1];
+  }
+  // x, step 1: codensity in, length-A DFTs over stride-B subsequences
 #pragma unroll
-    for (int k1 = 0; k1 < A; ++k1) sA[y * LD + k1 * B + n2] = tw_mul<false>(r[k1], tw[n2 * k1]);
+  for (int i = 0; i < G::X1_IT; ++i) {
+    const int it = t + i * NT;
+    if (it < N * B) {
+      const int n2 = it % B, y = it / B;
+      C r[A];
+#pragma unroll
+      for (int n1 = 0; n1 < A; ++n1) r[n1] = load(y, B * n1 + n2);
+      dft<A, false>(r);
+#pragma unroll
+      for (int k1 = 0; k1 < A; ++k1)
+        s0[y * LD + k1 * S + n2] = tw_mul<false>(r[k1], G::REG_TW ? twr[k1] : tw[n2 * k1]);
+    }
   }
   __syncthreads();
-#pragma unroll 1
-  for (int it = threadIdx.x; it < N * A; it += NT) {
-    const int k1 = it % A, y = it / A;
-    C r[B];
+  // x, step 2: length-B DFTs, output at natural f_x positions
+  if constexpr (G::DB) {
 #pragma unroll
-    for (int n2 = 0; n2 < B; ++n2) r[n2] = sA[y * LD + k1 * B + n2];
-    dft<B, false>(r);
+    for (int i = 0; i < G::X2_IT; ++i) {
+      const int it = t + i * NT;
+      if (it < N * A) {
+        int k1, row;
+        x2_item<A>(it, k1, row);
+        C r[B];
 #pragma unroll
-    for (int k2 = 0; k2 < B; ++k2) sA[y * LD + k1 * B + k2] = r[k2];
+        for (int n2 = 0; n2 < B; ++n2) r[n2] = s0[row * LD + k1 * S + n2];
+        dft<B, false>(r);
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) sy[row * LD + k1 + A * k2] = r[k2];
+      }
+    }
+  } else {
+    // one buffer: each iteration covers whole rows (NT is a multiple of 4 rows
+    // of A items), so its outputs are held in registers across one barrier
+#pragma unroll
+    for (int i = 0; i < G::X2_IT; ++i) {
+      const int it = t + i * NT;
+      int k1 = 0, row = 0;
+      C hold[B];
+      if (it < N * A) {
+        x2_item<A>(it, k1, row);
+#pragma unroll
+        for (int n2 = 0; n2 < B; ++n2) hold[n2] = s0[row * LD + k1 * S + n2];
+        dft<B, false>(hold);
+      }
+      __syncthreads();
+      if (it < N * A) {
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) sy[row * LD + k1 + A * k2] = hold[k2];
+      }
+    }
   }
   __syncthreads();
+  // y, step 1: warp-uniform n2, lanes over kept f_x columns; in place
+  const int nkb = (P1 + 31) >> 5;
 #pragma unroll 1
-  for (int it = threadIdx.x; it < P1 * B; it += NT) {
-    const int kxb = it % P1, n2 = it / P1;
-    const int fx = idx_of_box(kxb, N, h1);
-    const int col = (fx % A) * B + fx / A;
-    C r[A];
+  for (int u = warp; u < B * nkb; u += NW) {
+    const int n2 = u % B, kxb = lane + 32 * (u / B);
+    if (kxb < P1) {
+      const int fx = idx_of_box(kxb, N, h1);
+      C r[A];
 #pragma unroll
-    for (int n1 = 0; n1 < A; ++n1) r[n1] = sA[(B * n1 + n2) * LD + col];
-    dft<A, false>(r);
+      for (int n1 = 0; n1 < A; ++n1) r[n1] = sy[(B * n1 + n2) * LD + fx];
+      dft<A, false>(r);
 #pragma unroll
-    for (int k1 = 0; k1 < A; ++k1) sA[(k1 * B + n2) * LD + col] = tw_mul<false>(r[k1], tw[n2 * k1]);
+      for (int k1 = 0; k1 < A; ++k1) sy[(k1 * B + n2) * LD + fx] = tw_mul<false>(r[k1], tw[n2 * k1]);
+    }
   }
   __syncthreads();
+  // y, step 2: warp-uniform k1; kept f_y go to store
 #pragma unroll 1
-  for (int it = threadIdx.x; it < P1 * A; it += NT) {
-    const int kxb = it % P1, k1 = it / P1;
-    const int fx = idx_of_box(kxb, N, h1);
-    const int col = (fx % A) * B + fx / A;
-    C r[B];
+  for (int u = warp; u < A * nkb; u += NW) {
+    const int k1 = u % A, kxb = lane + 32 * (u / A);
+    if (kxb < P1) {
+      const int fx = idx_of_box(kxb, N, h1);
+      C r[B];
 #pragma unroll
-    for (int n2 = 0; n2 < B; ++n2) r[n2] = sA[(k1 * B + n2) * LD + col];
-    dft<B, false>(r);
+      for (int n2 = 0; n2 < B; ++n2) r[n2] = sy[(k1 * B + n2) * LD + fx];
+      dft<B, false>(r);
 #pragma unroll
-    for (int k2 = 0; k2 < B; ++k2) {
-      const int k = k1 + A * k2;
-      if (kept(k, N, h2)) store(box_of(k, N, h2), kxb, r[k2]);
+      for (int k2 = 0; k2 < B; ++k2) {
+        const int k = k1 + A * k2;
+        if (kept(k, N, h2)) store(box_of(k, N, h2), kxb, r[k2]);
+      }
     }
   }
   __syncthreads();
 }
 
-// Inverse y then x transform of one plane from kept frequencies
-// (load(kyb, kxb)) to the full real-space plane, in place in sA.  Every output
-// goes to consume(i, k2, y, x, value), where (i, k2) is a compile-time
-// register slot of the calling thread (fixed across calls).  After the y
-// transform, row y = k1 + A*k2 sits in sA row k1*B + k2.
-template <int N, int NT, typename T, typename Load, typename Consume>
-__device__ __forceinline__ void plane_inverse(const cplx<T>* tw, cplx<T>* sA, int h1, int P1,
-                                              int h2, Load load, Consume consume) {
+// Inverse y then x transform from kept frequencies (load(kyb, kxb)) to the
+// full real-space plane.  Every output goes to consume(i, k2, y, x, value),
+// where (i, k2) is a compile-time register slot of the calling thread (fixed
+// across calls).  After the y transform, row y = k1 + A*k2 sits in row
+// k1*B + k2 of the natural-order buffer.
+// tw2 is the [k1][n2] table of W_N^(n2*k1) (make_twiddles2), read by the x
+// step whenever its twiddles are not kept in registers; callers always pass it.
+template <int N, typename T, bool TWREG, typename Load, typename Consume>
+__device__ __forceinline__ void plane_inverse(const cplx<T>* tw, const cplx<T>* tw2, cplx<T>* s0,
+                                              cplx<T>* s1, int h1, int P1, int h2, Load load,
+                                              Consume consume, const void* pf_x = nullptr,
+                                              long long pf_x_bytes = 0, const void* pf_next = nullptr,
+                                              long long pf_next_bytes = 0) {
   using C = cplx<T>;
-  constexpr int A = Fac<N>::A, B = Fac<N>::B, LD = N + 1;
-  constexpr int IPT = (N * A + NT - 1) / NT;
-#pragma unroll 1
-  for (int it = threadIdx.x; it < P1 * B; it += NT) {
-    const int kxb = it % P1, n2 = it / P1;
-    const int xm = idx_of_box(kxb, N, h1);
-    C r[A];
+  using G = PlaneCfg<N, T>;
+  constexpr int A = G::A, B = G::B, S = G::S, LD = G::LD, NT = G::NT, NW = G::NW;
+  constexpr bool REG = TWREG && G::REG_TW;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  C* sx = G::DB ? s1 : s0;   // buffer of the slot-order x exchange
+  C twr[REG ? A : 1];
+  if constexpr (REG) {
 #pragma unroll
-    for (int n1 = 0; n1 < A; ++n1) {
-      const int m = B * n1 + n2;
-      r[n1] = kept(m, N, h2) ? load(box_of(m, N, h2), kxb) : czero<C>();
+    for (int k1 = 0; k1 < A; ++k1) twr[k1] = tw[(t % B) * k1];
+  }
+  const int nkb = (P1 + 31) >> 5;
+  // y, step 1: kept f_y in, warp-uniform n2, lanes over kept f_x
+#pragma unroll 1
+  for (int u = warp; u < B * nkb; u += NW) {
+    const int n2 = u % B, kxb = lane + 32 * (u / B);
+    if (kxb < P1) {
+      const int xm = idx_of_box(kxb, N, h1);
+      C r[A];
+#pragma unroll
+      for (int n1 = 0; n1 < A; ++n1) {
+        const int m = B * n1 + n2;
+        r[n1] = kept(m, N, h2) ? load(box_of(m, N, h2), kxb) : czero<C>();
+      }
+      dft<A, true>(r);
+#pragma unroll
+      for (int k1 = 0; k1 < A; ++k1) s0[(k1 * B + n2) * LD + xm] = tw_mul<true>(r[k1], tw[n2 * k1]);
     }
-    dft<A, true>(r);
-#pragma unroll
-    for (int k1 = 0; k1 < A; ++k1) sA[(k1 * B + n2) * LD + xm] = tw_mul<true>(r[k1], tw[n2 * k1]);
   }
   __syncthreads();
+  // y, step 2: warp-uniform k1, in place (row y = k1 + A*k2 lands in row k1*B + k2)
 #pragma unroll 1
-  for (int it = threadIdx.x; it < P1 * A; it += NT) {
-    const int kxb = it % P1, k1 = it / P1;
-    const int xm = idx_of_box(kxb, N, h1);
-    C r[B];
+  for (int u = warp; u < A * nkb; u += NW) {
+    const int k1 = u % A, kxb = lane + 32 * (u / A);
+    if (kxb < P1) {
+      const int xm = idx_of_box(kxb, N, h1);
+      C r[B];
 #pragma unroll
-    for (int n2 = 0; n2 < B; ++n2) r[n2] = sA[(k1 * B + n2) * LD + xm];
-    dft<B, true>(r);
+      for (int n2 = 0; n2 < B; ++n2) r[n2] = s0[(k1 * B + n2) * LD + xm];
+      dft<B, true>(r);
 #pragma unroll
-    for (int k2 = 0; k2 < B; ++k2) sA[(k1 * B + k2) * LD + xm] = r[k2];
-  }
-  __syncthreads();
-#pragma unroll 1
-  for (int it = threadIdx.x; it < N * B; it += NT) {
-    const int n2 = it % B, row = it / B;
-    C r[A];
-#pragma unroll
-    for (int n1 = 0; n1 < A; ++n1) {
-      const int m = B * n1 + n2;
-      r[n1] = kept(m, N, h1) ? sA[row * LD + m] : czero<C>();
+      for (int k2 = 0; k2 < B; ++k2) s0[(k1 * B + k2) * LD + xm] = r[k2];
     }
-    dft<A, true>(r);
-#pragma unroll
-    for (int k1 = 0; k1 < A; ++k1) sA[row * LD + k1 * B + n2] = tw_mul<true>(r[k1], tw[n2 * k1]);
   }
   __syncthreads();
+  // optional L1 prefetch of what the last step reads (pass C: the u_j plane)
+  if (pf_x) prefetch_l1(pf_x, pf_x_bytes);
+  // x, step 1: kept f_x of every row in, slot-order out
+  if constexpr (G::DB) {
 #pragma unroll
-  for (int i = 0; i < IPT; ++i) {
-    const int it = threadIdx.x + i * NT;
+    for (int i = 0; i < G::X1_IT; ++i) {
+      const int it = t + i * NT;
+      if (it < N * B) {
+        const int n2 = it % B, row = it / B;
+        C r[A];
+#pragma unroll
+        for (int n1 = 0; n1 < A; ++n1) {
+          const int m = B * n1 + n2;
+          r[n1] = kept(m, N, h1) ? s0[row * LD + m] : czero<C>();
+        }
+        dft<A, true>(r);
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) {
+          C w;
+          if constexpr (REG) w = twr[k1]; else w = tw2[k1 * B + n2];
+          sx[row * LD + k1 * S + n2] = tw_mul<true>(r[k1], w);
+        }
+      }
+    }
+  } else {
+    // one buffer: each iteration covers whole rows (NT is a multiple of B), so
+    // its outputs are held in registers across one barrier
+#pragma unroll
+    for (int i = 0; i < G::X1_IT; ++i) {
+      const int it = t + i * NT;
+      const int n2 = it % B, row = it / B;
+      C hold[A];
+      if (it < N * B) {
+#pragma unroll
+        for (int n1 = 0; n1 < A; ++n1) {
+          const int m = B * n1 + n2;
+          hold[n1] = kept(m, N, h1) ? s0[row * LD + m] : czero<C>();
+        }
+        dft<A, true>(hold);
+      }
+      __syncthreads();
+      if (it < N * B) {
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) {
+          C w;
+          if constexpr (REG) w = twr[k1]; else w = tw2[k1 * B + n2];
+          sx[row * LD + k1 * S + n2] = tw_mul<true>(hold[k1], w);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // optional L1 prefetch of the next call's input (pass C: the next plane)
+  if (pf_next) prefetch_l1(pf_next, pf_next_bytes);
+  // x, step 2: every output to consume
+#pragma unroll
+  for (int i = 0; i < G::X2_IT; ++i) {
+    const int it = t + i * NT;
     if (it < N * A) {
-      const int k1 = it % A, row = it / A;
+      int k1, row;
+      x2_item<A>(it, k1, row);
       const int y = row / B + A * (row % B);
       C r[B];
 #pragma unroll
-      for (int n2 = 0; n2 < B; ++n2) r[n2] = sA[row * LD + k1 * B + n2];
+      for (int n2 = 0; n2 < B; ++n2) r[n2] = sx[row * LD + k1 * S + n2];
       dft<B, true>(r);
 #pragma unroll
       for (int k2 = 0; k2 < B; ++k2) consume(i, k2, y, k1 + A * k2, r[k2]);
@@ -199,69 +373,82 @@ __device__ __forceinline__ void plane_inverse(const cplx<T>* tw, cplx<T>* sA, in
   __syncthreads();
 }
 
-// Forward z transform of a row of width W (pencils indexed by c < W);
-// load(z, c) real space, out(kzb, c, value) for kept |f_z| <= h3.
+// Forward z transform of a row of W pencils: load(z, c) real space,
+// out(kzb, c, value) for the kept |f_z| <= h3.  Warp-uniform n2 / k1, lanes
+// over c, so shared accesses are bank-conflict free and twiddles broadcast.
 template <int N, int NT, typename T, typename Load, typename Out>
 __device__ __forceinline__ void pencil_forward(const cplx<T>* tw, cplx<T>* sZ, int W, int h3,
                                               Load load, Out out) {
   using C = cplx<T>;
-  constexpr int A = Fac<N>::A, B = Fac<N>::B;
+  constexpr int A = Lay<N>::A, B = Lay<N>::B, NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ncb = (W + 31) >> 5;
 #pragma unroll 1
-  for (int it = threadIdx.x; it < W * B; it += NT) {
-    const int c = it % W, n2 = it / W;
-    C r[A];
+  for (int u = warp; u < B * ncb; u += NW) {
+    const int n2 = u % B, c = lane + 32 * (u / B);
+    if (c < W) {
+      C r[A];
 #pragma unroll
-    for (int n1 = 0; n1 < A; ++n1) r[n1] = load(B * n1 + n2, c);
-    dft<A, false>(r);
+      for (int n1 = 0; n1 < A; ++n1) r[n1] = load(B * n1 + n2, c);
+      dft<A, false>(r);
 #pragma unroll
-    for (int k1 = 0; k1 < A; ++k1) sZ[(k1 * B + n2) * W + c] = tw_mul<false>(r[k1], tw[n2 * k1]);
+      for (int k1 = 0; k1 < A; ++k1) sZ[(k1 * B + n2) * W + c] = tw_mul<false>(r[k1], tw[n2 * k1]);
+    }
   }
   __syncthreads();
 #pragma unroll 1
-  for (int it = threadIdx.x; it < W * A; it += NT) {
-    const int c = it % W, k1 = it / W;
-    C r[B];
+  for (int u = warp; u < A * ncb; u += NW) {
+    const int k1 = u % A, c = lane + 32 * (u / A);
+    if (c < W) {
+      C r[B];
 #pragma unroll
-    for (int n2 = 0; n2 < B; ++n2) r[n2] = sZ[(k1 * B + n2) * W + c];
-    dft<B, false>(r);
+      for (int n2 = 0; n2 < B; ++n2) r[n2] = sZ[(k1 * B + n2) * W + c];
+      dft<B, false>(r);
 #pragma unroll
-    for (int k2 = 0; k2 < B; ++k2) {
-      const int k = k1 + A * k2;
-      if (kept(k, N, h3)) out(box_of(k, N, h3), c, r[k2]);
+      for (int k2 = 0; k2 < B; ++k2) {
+        const int k = k1 + A * k2;
+        if (kept(k, N, h3)) out(box_of(k, N, h3), c, r[k2]);
+      }
     }
   }
 }
 
-// Inverse z transform of a row of width W from kept frequencies load(kzb, c)
-// to real space store(z, c, value).
+// Inverse z transform of a row of W pencils from kept frequencies
+// load(kzb, c) to real space store(z, c, value).
 template <int N, int NT, typename T, typename Load, typename Store>
 __device__ __forceinline__ void pencil_inverse(const cplx<T>* tw, cplx<T>* sZ, int W, int h3,
                                               Load load, Store store) {
   using C = cplx<T>;
-  constexpr int A = Fac<N>::A, B = Fac<N>::B;
+  constexpr int A = Lay<N>::A, B = Lay<N>::B, NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ncb = (W + 31) >> 5;
 #pragma unroll 1
-  for (int it = threadIdx.x; it < W * B; it += NT) {
-    const int c = it % W, n2 = it / W;
-    C r[A];
+  for (int u = warp; u < B * ncb; u += NW) {
+    const int n2 = u % B, c = lane + 32 * (u / B);
+    if (c < W) {
+      C r[A];
 #pragma unroll
-    for (int n1 = 0; n1 < A; ++n1) {
-      const int m = B * n1 + n2;
-      r[n1] = kept(m, N, h3) ? load(box_of(m, N, h3), c) : czero<C>();
+      for (int n1 = 0; n1 < A; ++n1) {
+        const int m = B * n1 + n2;
+        r[n1] = kept(m, N, h3) ? load(box_of(m, N, h3), c) : czero<C>();
+      }
+      dft<A, true>(r);
+#pragma unroll
+      for (int k1 = 0; k1 < A; ++k1) sZ[(k1 * B + n2) * W + c] = tw_mul<true>(r[k1], tw[n2 * k1]);
     }
-    dft<A, true>(r);
-#pragma unroll
-    for (int k1 = 0; k1 < A; ++k1) sZ[(k1 * B + n2) * W + c] = tw_mul<true>(r[k1], tw[n2 * k1]);
   }
   __syncthreads();
 #pragma unroll 1
-  for (int it = threadIdx.x; it < W * A; it += NT) {
-    const int c = it % W, k1 = it / W;
-    C r[B];
+  for (int u = warp; u < A * ncb; u += NW) {
+    const int k1 = u % A, c = lane + 32 * (u / A);
+    if (c < W) {
+      C r[B];
 #pragma unroll
-    for (int n2 = 0; n2 < B; ++n2) r[n2] = sZ[(k1 * B + n2) * W + c];
-    dft<B, true>(r);
+      for (int n2 = 0; n2 < B; ++n2) r[n2] = sZ[(k1 * B + n2) * W + c];
+      dft<B, true>(r);
 #pragma unroll
-    for (int k2 = 0; k2 < B; ++k2) store(k1 + A * k2, c, r[k2]);
+      for (int k2 = 0; k2 < B; ++k2) store(k1 + A * k2, c, r[k2]);
+    }
   }
 }
 
@@ -269,46 +456,51 @@ template <int N, typename T> __device__ __forceinline__ void load_twiddles(cplx<
   for (int i = threadIdx.x; i < N; i += blockDim.x) dst[i] = ((const cplx<T>*)src)[i];
 }
 
-// Shared-memory sizes (bytes) of each kernel.
-template <int N, typename T> constexpr size_t smem_plane() {
-  return sizeof(cplx<T>) * ((size_t)N + (size_t)N * (N + 1));
+// tw2[k1 * B + n2] = tw[n2 * k1] (call after load_twiddles and a barrier)
+template <int N, typename T> __device__ __forceinline__ void make_twiddles2(cplx<T>* tw2, const cplx<T>* tw) {
+  constexpr int A = Lay<N>::A, B = Lay<N>::B;
+  for (int i = threadIdx.x; i < A * B; i += blockDim.x) tw2[i] = tw[(i % B) * (i / B)];
 }
+
 template <int N, typename T> constexpr size_t smem_pencil(int W, int P3) {
   return sizeof(cplx<T>) * ((size_t)N + (size_t)N * W + (size_t)P3 * W);
 }
 
 // ------------------------------------------------------------- the passes --
 
-// Pass A: grid (TA, N); CTA (ta, z) loops over the TJ occupied bands.
-template <int N, int NT, typename T>
-__global__ void __launch_bounds__(NT) k_pass_a(PairArgs p) {
+// Pass A: grid (TA, N); CTA (ta, z) loops over the TJ occupied bands.  One
+// plane buffer, so two CTAs share an SM and overlap each other's barriers.
+template <int N, typename T> using PassACfg = PlaneCfg<N, T, false>;
+template <int N, typename T>
+__global__ void __launch_bounds__(PassACfg<N, T>::NT, sizeof(T) == 4 ? 2 : 1) k_pass_a(PairArgs p) {
   using C = cplx<T>;
+  using G = PassACfg<N, T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
-  C* sA = tw + N;
+  C* s0 = tw + N;
+  C* s1 = s0 + G::BUF;
   load_twiddles<N, T>(tw, p.tw);
   __syncthreads();
   const int ta = blockIdx.x, z = blockIdx.y;
   constexpr long long plane = (long long)N * N;
   const C* ua = reinterpret_cast<const C*>(p.u_tgt) + ta * p.u_tgt_stride + z * plane;
+  const int P1 = p.P1;
 #pragma unroll 1
   for (int tj = 0; tj < p.TJ; ++tj) {
     const C* uj = reinterpret_cast<const C*>(p.u_occ) + tj * p.u_occ_stride + z * plane;
     C* out = reinterpret_cast<C*>(p.inter) +
              ((long long)(ta * p.TJ + tj) * N + z) * (long long)p.P2 * p.P1;
-    const int P1 = p.P1;
-    plane_forward<N, NT, T>(
-        tw, sA, p.h1, p.P1, p.h2,
+    plane_forward<N, T, false>(
+        tw, s0, s1, p.h1, p.P1, p.h2,
         [&](int y, int x) { return cmulc(uj[y * N + x], ua[y * N + x]); },
         [&](int kyb, int kxb, C v) { out[kyb * P1 + kxb] = v; });
-    __syncthreads();
   }
 }
 
 // Pass B: grid (P2, TA*TJ); CTA (kyb, pair) transforms its row along z,
 // multiplies by v(k - q + G)/N and transforms back, in place.
 template <int N, int NT, typename T>
-__global__ void __launch_bounds__(NT) k_pass_b(PairArgs p) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_pass_b(PairArgs p) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
@@ -366,22 +558,26 @@ __global__ void __launch_bounds__(NT) k_pass_b_dmu(PairArgs p) {
 
 // Pass C: grid (TA, N); CTA (ta, z) accumulates -(w_j/N_q) u_j W over the
 // occupied batch in registers and adds the plane into the FP64 accumulator.
-template <int N, int NT, typename T>
-__global__ void __launch_bounds__(NT) k_pass_c(PairArgs p) {
+template <int N, typename T>
+__global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_c(PairArgs p) {
   using C = cplx<T>;
-  constexpr int A = Fac<N>::A, B = Fac<N>::B;
-  constexpr int IPT = (N * A + NT - 1) / NT;
+  using G = PlaneCfg<N, T>;
+  constexpr int A = G::A, B = G::B, NT = G::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
-  C* sA = tw + N;
+  C* tw2 = tw + N;
+  C* s0 = tw2 + N;
+  C* s1 = s0 + G::BUF;
   load_twiddles<N, T>(tw, p.tw);
+  __syncthreads();
+  make_twiddles2<N, T>(tw2, tw);
   __syncthreads();
   const int ta = blockIdx.x, z = blockIdx.y;
   constexpr long long plane = (long long)N * N;
   const int P1 = p.P1;
-  C acc[IPT][B];
+  C acc[G::X2_IT][B];
 #pragma unroll
-  for (int i = 0; i < IPT; ++i)
+  for (int i = 0; i < G::X2_IT; ++i)
 #pragma unroll
     for (int k2 = 0; k2 < B; ++k2) acc[i][k2] = czero<C>();
 #pragma unroll 1
@@ -390,21 +586,25 @@ __global__ void __launch_bounds__(NT) k_pass_c(PairArgs p) {
                   ((long long)(ta * p.TJ + tj) * N + z) * (long long)p.P2 * p.P1;
     const C* uj = reinterpret_cast<const C*>(p.u_occ) + tj * p.u_occ_stride + z * plane;
     const T cf = (T)(p.coef * p.w_occ[tj]);
-    plane_inverse<N, NT, T>(
-        tw, sA, p.h1, p.P1, p.h2, [&](int kyb, int kxb) { return in[kyb * P1 + kxb]; },
+    const long long pbytes = (long long)p.P2 * p.P1 * (long long)sizeof(C);
+    const C* next = tj + 1 < p.TJ ? in + (long long)N * p.P2 * p.P1 : nullptr;
+    plane_inverse<N, T, false>(
+        tw, tw2, s0, s1, p.h1, p.P1, p.h2, [&](int kyb, int kxb) { return in[kyb * P1 + kxb]; },
         [&](int i, int k2, int y, int x, C v) {
           const C t = cmul(uj[y * N + x], v);
           acc[i][k2].x += cf * t.x;
           acc[i][k2].y += cf * t.y;
-        });
+        },
+        uj, plane * (long long)sizeof(C), next, pbytes);
   }
   double2* dst = p.acc + ta * plane * N + z * plane;
 #pragma unroll
-  for (int i = 0; i < IPT; ++i) {
+  for (int i = 0; i < G::X2_IT; ++i) {
     const int it = threadIdx.x + i * NT;
     if (it < N * A) {
       // same slot -> (y, x) map as plane_inverse's last step
-      const int k1 = it % A, row = it / A;
+      int k1, row;
+      x2_item<A>(it, k1, row);
       const int y = row / B + A * (row % B);
 #pragma unroll
       for (int k2 = 0; k2 < B; ++k2) {
@@ -488,39 +688,46 @@ __global__ void __launch_bounds__(NT) k_s2g_z(GridArgs g) {
 }
 
 // grid (nb, N): inverse y and x transforms of stage plane (b, z) into u[b][z]
-template <int N, int NT, typename T>
-__global__ void __launch_bounds__(NT) k_s2g_xy(GridArgs g) {
+template <int N, typename T>
+__global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_s2g_xy(GridArgs g) {
   using C = cplx<T>;
+  using G = PlaneCfg<N, T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
-  C* sA = tw + N;
+  C* tw2 = tw + N;
+  C* s0 = tw2 + N;
+  C* s1 = s0 + G::BUF;
   load_twiddles<N, T>(tw, g.tw);
+  __syncthreads();
+  make_twiddles2<N, T>(tw2, tw);
   __syncthreads();
   const int b = blockIdx.x, z = blockIdx.y;
   const int Q1 = g.Q1, Q2 = g.Q2;
   const C* st = reinterpret_cast<const C*>(g.stage) + ((long long)b * N + z) * Q2 * Q1;
   C* u = reinterpret_cast<C*>(g.u) + (long long)b * N * N * N + (long long)z * N * N;
   const T sc = (T)g.scale;
-  plane_inverse<N, NT, T>(
-      tw, sA, g.n1, Q1, g.n2, [&](int kyb, int kxb) { return st[kyb * Q1 + kxb]; },
+  plane_inverse<N, T, true>(
+      tw, tw2, s0, s1, g.n1, Q1, g.n2, [&](int kyb, int kxb) { return st[kyb * Q1 + kxb]; },
       [&](int, int, int y, int x, C v) { u[y * N + x] = sc * v; });
 }
 
 // grid (nb, N): forward x and y transforms of FP64 grid plane (b, z) into stage
-template <int N, int NT>
-__global__ void __launch_bounds__(NT) k_g2s_xy(GridArgs g) {
+template <int N>
+__global__ void __launch_bounds__(PlaneCfg<N, double>::NT) k_g2s_xy(GridArgs g) {
   using C = double2;
+  using G = PlaneCfg<N, double>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
-  C* sA = tw + N;
+  C* s0 = tw + N;
+  C* s1 = s0 + G::BUF;
   load_twiddles<N, double>(tw, g.tw);
   __syncthreads();
   const int b = blockIdx.x, z = blockIdx.y;
   const int Q1 = g.Q1;
   const C* f = g.f + (long long)b * N * N * N + (long long)z * N * N;
   C* st = reinterpret_cast<C*>(g.stage) + ((long long)b * N + z) * g.Q2 * Q1;
-  plane_forward<N, NT, double>(
-      tw, sA, g.n1, Q1, g.n2, [&](int y, int x) { return f[y * N + x]; },
+  plane_forward<N, double, PlaneCfg<N, double>::DB>(
+      tw, s0, s1, g.n1, Q1, g.n2, [&](int y, int x) { return f[y * N + x]; },
       [&](int kyb, int kxb, C v) { st[kyb * Q1 + kxb] = v; });
 }
 

@@ -33,9 +33,10 @@ template <typename K> inline void allow_smem(K kernel, size_t bytes) {
 }
 
 template <int N, typename T> void launch_pass_a(const PairArgs& p, cudaStream_t s) {
-  const size_t sm = smem_plane<N, T>();
-  allow_smem(k_pass_a<N, kThreads, T>, sm);
-  k_pass_a<N, kThreads, T><<<dim3(p.TA, N), kThreads, sm, s>>>(p);
+  using G = PassACfg<N, T>;
+  const size_t sm = G::smem();
+  allow_smem(k_pass_a<N, T>, sm);
+  k_pass_a<N, T><<<dim3(p.TA, N), G::NT, sm, s>>>(p);
 }
 template <int N, typename T> void launch_pass_b(const PairArgs& p, cudaStream_t s) {
   const size_t sm = smem_pencil<N, T>(p.P1, p.P3);
@@ -48,9 +49,10 @@ template <int N, typename T> void launch_pass_b_dmu(const PairArgs& p, cudaStrea
   k_pass_b_dmu<N, kThreads, T><<<dim3(p.P2, p.TA * p.TJ), kThreads, sm, s>>>(p);
 }
 template <int N, typename T> void launch_pass_c(const PairArgs& p, cudaStream_t s) {
-  const size_t sm = smem_plane<N, T>();
-  allow_smem(k_pass_c<N, kThreads, T>, sm);
-  k_pass_c<N, kThreads, T><<<dim3(p.TA, N), kThreads, sm, s>>>(p);
+  using G = PlaneCfg<N, T>;
+  const size_t sm = G::smem();
+  allow_smem(k_pass_c<N, T>, sm);
+  k_pass_c<N, T><<<dim3(p.TA, N), G::NT, sm, s>>>(p);
 }
 template <int N, typename T> void launch_s2g_z(const GridArgs& g, cudaStream_t s) {
   const size_t sm = smem_pencil<N, T>(g.Q1, 0);
@@ -58,14 +60,16 @@ template <int N, typename T> void launch_s2g_z(const GridArgs& g, cudaStream_t s
   k_s2g_z<N, kThreads, T><<<dim3(g.Q2, g.nb), kThreads, sm, s>>>(g);
 }
 template <int N, typename T> void launch_s2g_xy(const GridArgs& g, cudaStream_t s) {
-  const size_t sm = smem_plane<N, T>();
-  allow_smem(k_s2g_xy<N, kThreads, T>, sm);
-  k_s2g_xy<N, kThreads, T><<<dim3(g.nb, N), kThreads, sm, s>>>(g);
+  using G = PlaneCfg<N, T>;
+  const size_t sm = G::smem();
+  allow_smem(k_s2g_xy<N, T>, sm);
+  k_s2g_xy<N, T><<<dim3(g.nb, N), G::NT, sm, s>>>(g);
 }
 template <int N> void launch_g2s_xy(const GridArgs& g, cudaStream_t s) {
-  const size_t sm = smem_plane<N, double>();
-  allow_smem(k_g2s_xy<N, kThreads>, sm);
-  k_g2s_xy<N, kThreads><<<dim3(g.nb, N), kThreads, sm, s>>>(g);
+  using G = PlaneCfg<N, double>;
+  const size_t sm = G::smem();
+  allow_smem(k_g2s_xy<N>, sm);
+  k_g2s_xy<N><<<dim3(g.nb, N), G::NT, sm, s>>>(g);
 }
 template <int N> void launch_g2s_z(const GridArgs& g, cudaStream_t s) {
   const size_t sm = smem_pencil<N, double>(g.Q1, 0);
