@@ -181,6 +181,30 @@ int xx_energy_from_vx_range(xx_plan plan, int k_first, int k_count, const void *
 int xx_apply_backward(xx_plan plan, const void *c, const double *w, int n_b, const void *vx,
                       double grad_ex, void *dc_out, double *dmu_out, void *stream);
 
+/* One independent exchange job for xx_run_many. */
+typedef struct {
+  xx_plan plan;             /* each job needs its own plan (workspace) */
+  const void *c_occ;        /* as xx_energy */
+  int ld_occ;
+  const double *w_occ;
+  int n_occ;
+  const void *c_tgt;
+  const double *w_tgt;      /* may be NULL when ex_out is NULL */
+  int n_tgt;
+  void *vx_out;
+  double *ex_out;           /* device double[2], or NULL for V_x c only */
+} xx_job;
+
+/*
+ * Run independent jobs (different cells, grids or k-meshes, one plan each)
+ * concurrently, as the paper does with CUDA streams for small structures:
+ * each job runs on its plan's own stream, which first waits for the work
+ * already queued on `stream`; `stream` then waits for every job.  Results are
+ * identical to running the jobs one after another.  Returns the first failing
+ * job's status (XX_ERR_INVALID_ARGUMENT if two jobs share a plan).
+ */
+int xx_run_many(int n_jobs, const xx_job *jobs, void *stream);
+
 /*
  * Wait for the plan's work on stream with a time limit (seconds, <= 0 waits
  * without limit), then report the device error flag.  Returns XX_OK,

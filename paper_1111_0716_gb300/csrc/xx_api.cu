@@ -209,6 +209,9 @@ struct xx_plan_s {
   struct Rec { int cls; int e0, e1; };
   std::vector<Rec> recs;
   size_t ev_next = 0;
+  // own stream and join events for xx_run_many
+  cudaStream_t own_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -709,6 +712,9 @@ int xx_destroy(xx_plan p) {
   if (p->d_tw64) cudaFree(p->d_tw64);
   if (p->d_err) cudaFree(p->d_err);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->own_stream) cudaStreamDestroy(p->own_stream);
   delete p;
   return XX_OK;
 }
@@ -800,6 +806,50 @@ int xx_apply_backward(xx_plan p, const void* c, const double* w, int n_b, const 
   }
   if (dmu_out) return run_dmu(p, c, w, n_b, grad_ex, dmu_out, s);
   return XX_OK;
+}
+
+int xx_run_many(int n_jobs, const xx_job* jobs, void* stream) {
+  if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return XX_ERR_INVALID_ARGUMENT;
+  for (int i = 0; i < n_jobs; ++i) {
+    if (!jobs[i].plan) return XX_ERR_INVALID_ARGUMENT;
+    for (int j = 0; j < i; ++j)
+      if (jobs[j].plan == jobs[i].plan) return XX_ERR_INVALID_ARGUMENT;
+  }
+  cudaStream_t caller = (cudaStream_t)stream;
+  // fork: every job's stream waits for the caller's queued work
+  for (int i = 0; i < n_jobs; ++i) {
+    xx_plan p = jobs[i].plan;
+    cudaError_t e = cudaSuccess;
+    if (!p->own_stream) e = cudaStreamCreateWithFlags(&p->own_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !p->ev_fork) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !p->ev_join) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_fork, caller);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->own_stream, p->ev_fork, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_status(e);
+    }
+  }
+  int status = XX_OK;
+  for (int i = 0; i < n_jobs; ++i) {
+    const xx_job& j = jobs[i];
+    xx_plan p = j.plan;
+    int st;
+    if (j.ex_out)
+      st = xx_energy(p, j.c_occ, j.ld_occ, j.w_occ, j.n_occ, j.c_tgt, j.w_tgt, j.n_tgt, j.vx_out,
+                     j.ex_out, p->own_stream);
+    else
+      st = xx_apply(p, j.c_occ, j.ld_occ, j.w_occ, j.n_occ, j.c_tgt, j.n_tgt, j.vx_out, p->own_stream);
+    if (st != XX_OK && status == XX_OK) status = st;
+  }
+  // join: the caller's stream waits for every job
+  for (int i = 0; i < n_jobs; ++i) {
+    xx_plan p = jobs[i].plan;
+    cudaError_t e = cudaEventRecord(p->ev_join, p->own_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, p->ev_join, 0);
+    if (e != cudaSuccess && status == XX_OK) status = cuda_status(e);
+  }
+  return status;
 }
 
 int xx_sync(xx_plan p, void* stream, double timeout_s) {

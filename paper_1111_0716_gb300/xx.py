@@ -36,7 +36,8 @@ XX_NOALLOC_MAX_ROWS = 16384
 EXPORTS = ("xx_create", "xx_destroy", "xx_apply", "xx_apply_range", "xx_energy",
            "xx_energy_range", "xx_energy_from_vx", "xx_energy_from_vx_range",
            "xx_apply_backward", "xx_sync", "xx_set_batch", "xx_profile_enable",
-           "xx_profile_read", "xx_plan_info", "xx_status_string", "xx_energy_from_vx_noalloc")
+           "xx_profile_read", "xx_plan_info", "xx_status_string", "xx_energy_from_vx_noalloc",
+           "xx_run_many")
 
 PROF_CLASSES = ("pass_a", "pass_b", "pass_c", "sphere_to_grid", "grid_to_sphere",
                 "kernel_table", "reduce", "pass_b_dmu")
@@ -47,6 +48,13 @@ class XXError(RuntimeError):
         self.status = status
         super().__init__("%s failed: %s (%s)" % (where, STATUS.get(status, status),
                                                   xx_status_string(status)))
+
+
+class xx_job(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("c_occ", ctypes.c_void_p), ("ld_occ", ctypes.c_int),
+                ("w_occ", ctypes.c_void_p), ("n_occ", ctypes.c_int), ("c_tgt", ctypes.c_void_p),
+                ("w_tgt", ctypes.c_void_p), ("n_tgt", ctypes.c_int), ("vx_out", ctypes.c_void_p),
+                ("ex_out", ctypes.c_void_p)]
 
 
 class xx_info(ctypes.Structure):
@@ -86,6 +94,7 @@ def load(path: Optional[str] = None):
     lib.xx_profile_enable.argtypes = [P, I]
     lib.xx_profile_read.argtypes = [P, P, P, I, I]
     lib.xx_energy_from_vx_noalloc.argtypes = [I, I, I, P, P, P, P, P, P]
+    lib.xx_run_many.argtypes = [I, ctypes.POINTER(xx_job), P]
     lib.xx_status_string.argtypes = [I]
     lib.xx_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -194,6 +203,27 @@ def xx_apply_backward(plan, c, w, n_b, vx, grad_ex, dc_out, dmu_out, stream=None
     _check(load().xx_apply_backward(plan, _dptr(c), _dptr(w), int(n_b), _dptr(vx),
                                     float(grad_ex), _dptr(dc_out), _dptr(dmu_out),
                                     _stream_ptr(stream)), "xx_apply_backward")
+
+
+def xx_run_many(jobs, stream=None):
+    """jobs: list of dicts with keys plan (Plan), c_occ, w_occ, c_tgt, w_tgt, vx_out, ex_out
+    (ex_out/w_tgt optional) and optional ld_occ; the occupied set is the leading bands when
+    c_occ is c_tgt."""
+    arr = (xx_job * len(jobs))()
+    for i, j in enumerate(jobs):
+        n_occ = j["w_occ"].shape[1]
+        ld = j.get("ld_occ", j["c_occ"].shape[1])
+        arr[i].plan = j["plan"].handle
+        arr[i].c_occ = _dptr(j["c_occ"])
+        arr[i].ld_occ = int(ld)
+        arr[i].w_occ = _dptr(j["w_occ"])
+        arr[i].n_occ = int(n_occ)
+        arr[i].c_tgt = _dptr(j["c_tgt"])
+        arr[i].w_tgt = _dptr(j.get("w_tgt"))
+        arr[i].n_tgt = int(j["c_tgt"].shape[1])
+        arr[i].vx_out = _dptr(j["vx_out"])
+        arr[i].ex_out = _dptr(j.get("ex_out"))
+    _check(load().xx_run_many(len(jobs), arr, _stream_ptr(stream)), "xx_run_many")
 
 
 def xx_sync(plan, stream=None, timeout_s: float = 0.0):

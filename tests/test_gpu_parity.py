@@ -182,3 +182,26 @@ def test_precision_sweep_cells(gpu, oracle_mod, i, kernel):
     vx64, _, _ = gu.run(wl, 1, shared=False, c_tgt=wl.c_tgt[:, [0, wl.n_tgt - 1]],
                         w_tgt=wl.w_tgt[:, [0, wl.n_tgt - 1]])
     assert gu.rel_max(vx64[0], ref) <= gu.FP64_TOL
+
+
+def test_run_many_sweep_cells_match_single_runs(gpu):
+    """The six sweep cells as one xx_run_many call (concurrent streams) equal separate runs."""
+    torch, xx = gpu
+    cells = [synth.sweep_cell(i) for i in range(len(synth.SWEEP_GRIDS))]
+    plans, jobs = [], []
+    for wl in cells:
+        plan = xx.Plan.from_workload(wl, precision=0)
+        c = gu.dev(wl.c_tgt)
+        jobs.append({"plan": plan, "c_occ": c, "ld_occ": c.shape[1], "w_occ": gu.dev(wl.w_occ),
+                     "c_tgt": c, "w_tgt": gu.dev(wl.w_tgt), "vx_out": torch.empty_like(c),
+                     "ex_out": torch.empty(2, dtype=torch.float64, device="cuda")})
+        plans.append(plan)
+    xx.xx_run_many(jobs)
+    torch.cuda.synchronize()
+    for wl, job, plan in zip(cells, jobs, plans):
+        vx, (e, _), _ = gu.run(wl, 0)
+        assert np.array_equal(job["vx_out"].cpu().numpy(), vx)
+        assert float(job["ex_out"][0].item()) == e
+        plan.close()
+    with pytest.raises(xx.XXError):
+        xx.xx_run_many([jobs[0], dict(jobs[0])])
