@@ -220,6 +220,9 @@ def main():
                          "bands, all q) once and exit: the case ncu captures")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="precision of --profile-case")
+    ap.add_argument("--with-vjp", action="store_true",
+                    help="also time the vector-Jacobian product (xx_apply_vjp, both orbital "
+                         "sets) on 16 target bands of every k-point")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -403,6 +406,34 @@ def main():
                               % (nt, no, p_slice)}
         p64.close()
         p32.close()
+
+    if rank == 0 and args.with_vjp:
+        nt = 16
+        ct = torch.from_numpy(wl.c_tgt[:, :nt].copy()).cuda()
+        co = torch.from_numpy(wl.c_occ.copy()).cuda()
+        wo = torch.from_numpy(wl.w_occ.copy()).cuda()
+        ybar = torch.from_numpy(np.ascontiguousarray(wl.c_tgt[:, nt:2 * nt])).cuda()
+        pv = xx.Plan.from_workload(wl, precision=xx.XX_FP32_MIXED)
+        fwd = pv.apply(co, wo, ct)
+        pv.vjp(co, wo, ct, ybar)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        pv.apply(co, wo, ct, vx_out=fwd)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        t_f = g0.elapsed_time(g1) / 1e3
+        g0.record(stream)
+        pv.vjp(co, wo, ct, ybar)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        t_v = g0.elapsed_time(g1) / 1e3
+        pv.close()
+        p_slice = wl.nk * nt * wl.nk * wl.n_occ
+        line["vjp"] = {"value": p_slice / t_v, "unit": UNIT, "forward_same_slice": p_slice / t_f,
+                       "sample": "%d target bands x 8 k x 160 occupied x 8 q = %d pairs; the VJP "
+                                 "returns dL/dc_tgt* and dL/dc_occ*" % (nt, p_slice)}
 
     if rank == 0 and world == 1 and not args.no_baseline:
         r, dt, p_s, cores = run_oracle_sample(wl, args.oracle_occ)

@@ -206,6 +206,26 @@ typedef struct {
 int xx_run_many(int n_jobs, const xx_job *jobs, void *stream);
 
 /*
+ * Vector-Jacobian product of y = V_x[c_occ] c_tgt (xx_apply's output) for a
+ * real loss L with cotangent ybar = dL/dy* (Wirtinger; device complex128
+ * [nk][n_tgt][npw_max]).  Inputs as xx_apply.
+ *   grad_tgt_out (device complex128 [nk][n_tgt][npw_max], or NULL):
+ *       dL/dc_tgt* = V_x ybar (V_x is Hermitian; one more operator application).
+ *   grad_occ_out (device complex128 [nk][n_occ][npw_max], or NULL):
+ *       dL/dc_occ* through both places the occupied orbitals enter the loops
+ *       (the codensity conj(u_qj) u_ka and the multiplication by u_qj):
+ *       dL/dc_qj* = P_q[ -(w_qj/N_k) sum_{k,a} (ubar_ka conj(W_aj) + u_ka conj(Wbar_aj)) ]
+ *       with ubar the grids of ybar, W_aj the pair potential of (u_ka, u_qj) and
+ *       Wbar_aj that of (ubar_ka, u_qj).  Costs about two forward applications;
+ *       pair potentials are recomputed, never stored beyond one batch.
+ * When the same orbitals are both occupied and targets, the total gradient
+ * is the sum of the two outputs.  Occupations are treated as constants.
+ */
+int xx_apply_vjp(xx_plan plan, const void *c_occ, int ld_occ, const double *w_occ, int n_occ,
+                 const void *c_tgt, int n_tgt, const void *ybar, void *grad_tgt_out,
+                 void *grad_occ_out, void *stream);
+
+/*
  * Wait for the plan's work on stream with a time limit (seconds, <= 0 waits
  * without limit), then report the device error flag.  Returns XX_OK,
  * XX_ERR_TIMEOUT (the stream is still busy; nothing was cancelled),

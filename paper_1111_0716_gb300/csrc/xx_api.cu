@@ -200,7 +200,7 @@ struct xx_plan_s {
   void* d_tw32 = nullptr;
   void* d_tw64 = nullptr;
   int* d_err = nullptr;
-  DevBuf u_tgt, u_occ, inter, acc, vt, dvt, box, stage, dots, partial, dmu_acc, vx_tmp;
+  DevBuf u_tgt, u_occ, inter, acc, vt, dvt, box, stage, dots, partial, dmu_acc, vx_tmp, u_bar;
   size_t ws_bytes = 0, peak_bytes = 0;
   long long launches = 0;
   // optional per-kernel-class timing with events on the launch stream
@@ -571,6 +571,64 @@ int run_dmu(xx_plan p, const void* c, const double* w, int n_b, double grad, dou
   return launched(p, 1);
 }
 
+// Occupied-orbital part of the vector-Jacobian product of y = V_x[c_occ] c_tgt
+// for a cotangent ybar = dL/dy* (Wirtinger):
+//   dL/dc_qj* = P_q[ -(w_qj/N_k) sum_{k,a} ( ubar_ka conj(W_aj) + u_ka conj(Wbar_aj) ) ]
+// with W_aj = K(conj(u_qj) u_ka), Wbar_aj = K(conj(u_qj) ubar_ka), ubar the
+// grids of ybar and P_q the grid->sphere projection of q.
+int run_vjp_occ(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, int n_occ,
+                const void* c_tgt, int n_tgt, const void* ybar, void* grad_occ, cudaStream_t s) {
+  const bool shared = (c_occ == c_tgt && ld_occ == n_tgt);
+  int st = build_grids(p, 0, p->nk, c_occ, ld_occ, n_occ, c_tgt, n_tgt, shared, s);
+  if (st) return st;
+  const size_t eb = elem_bytes(p);
+  if ((st = ensure(p, p->u_bar, (size_t)p->nk * n_tgt * n3(p) * eb))) return st;
+  for (int k = 0; k < p->nk; ++k) {
+    st = sphere_to_grid(p, k, (const double2*)ybar + (long long)k * n_tgt * p->npw_max, n_tgt,
+                        (char*)p->u_bar.p + (size_t)k * n_tgt * n3(p) * eb, s);
+    if (st) return st;
+  }
+  int TA, TJ;
+  batch_shape(p, n_tgt, n_occ, &TA, &TJ);
+  if ((st = ensure(p, p->inter, (size_t)TA * TJ * p->N * P(p, 1) * P(p, 0) * eb))) return st;
+  if ((st = ensure(p, p->acc, (size_t)n_occ * n3(p) * 16))) return st;
+  const KernelSet& ks = kset(p);
+  for (int q = 0; q < p->nk; ++q) {
+    cudaMemsetAsync(p->acc.p, 0, (size_t)n_occ * n3(p) * 16, s);
+    for (int k = 0; k < p->nk; ++k) {
+      if ((st = kernel_table_for(p, k, q, false, s))) return st;
+      for (int a0 = 0; a0 < n_tgt; a0 += TA) {
+        const int ta = (n_tgt - a0) < TA ? (n_tgt - a0) : TA;
+        for (int j0 = 0; j0 < n_occ; j0 += TJ) {
+          const int tj = (n_occ - j0) < TJ ? (n_occ - j0) : TJ;
+          const char* ut = grid_ptr(p, true, k, a0, n_occ, n_tgt);
+          const char* ub = (const char*)p->u_bar.p + ((size_t)k * n_tgt + a0) * n3(p) * eb;
+          PairArgs a = pair_args(p, ta, tj);
+          a.u_occ = grid_ptr(p, shared, q, j0, n_occ, n_tgt);
+          a.acc = (double2*)p->acc.p + (long long)j0 * n3(p);
+          a.w_occ = w_occ + (long long)q * n_occ + j0;
+          // term 1: W_aj from (u_a, u_j), multiplied by ubar_a
+          a.u_tgt = ut;
+          ks.pass_a(a, s);
+          ks.pass_b(a, s);
+          a.u_tgt = ub;
+          ks.pass_ct(a, s);
+          // term 2: Wbar_aj from (ubar_a, u_j), multiplied by u_a
+          ks.pass_a(a, s);
+          ks.pass_b(a, s);
+          a.u_tgt = ut;
+          ks.pass_ct(a, s);
+          if ((st = launched(p, 6))) return st;
+        }
+      }
+    }
+    st = grid_to_sphere(p, q, (const double2*)p->acc.p, n_occ,
+                        (double2*)grad_occ + (long long)q * n_occ * p->npw_max, s);
+    if (st) return st;
+  }
+  return XX_OK;
+}
+
 bool supported_grid(const int* g) { return g[0] == g[1] && g[1] == g[2] && supported_n(g[0]); }
 
 }  // namespace
@@ -704,7 +762,7 @@ int xx_destroy(xx_plan p) {
   if (!p) return XX_OK;
   cudaDeviceSynchronize();
   DevBuf* bufs[] = {&p->u_tgt, &p->u_occ, &p->inter, &p->acc, &p->vt, &p->dvt, &p->box,
-                    &p->stage, &p->dots, &p->partial, &p->dmu_acc, &p->vx_tmp};
+                    &p->stage, &p->dots, &p->partial, &p->dmu_acc, &p->vx_tmp, &p->u_bar};
   for (DevBuf* b : bufs) release(*b);
   if (p->d_miller) cudaFree(p->d_miller);
   if (p->d_npw) cudaFree(p->d_npw);
@@ -850,6 +908,32 @@ int xx_run_many(int n_jobs, const xx_job* jobs, void* stream) {
     if (e != cudaSuccess && status == XX_OK) status = cuda_status(e);
   }
   return status;
+}
+
+int xx_apply_vjp(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, int n_occ,
+                 const void* c_tgt, int n_tgt, const void* ybar, void* grad_tgt_out,
+                 void* grad_occ_out, void* stream) {
+  if (!p || n_occ < 0 || n_tgt < 0) return XX_ERR_INVALID_ARGUMENT;
+  if (ld_occ == 0) ld_occ = n_occ;
+  if (ld_occ < n_occ) return XX_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_tgt > 0 && bad_ptr(ybar)) return XX_ERR_INVALID_ARGUMENT;
+  const void* outs[2] = {grad_tgt_out, grad_occ_out};
+  for (const void* o : outs)
+    if (o && (o == c_occ || o == c_tgt || o == ybar)) return XX_ERR_INVALID_ARGUMENT;
+  int st;
+  if (grad_tgt_out && n_tgt > 0) {
+    // V_x is Hermitian: dL/dc_tgt* = V_x ybar
+    if ((st = xx_apply(p, c_occ, ld_occ, w_occ, n_occ, ybar, n_tgt, grad_tgt_out, stream))) return st;
+  }
+  if (grad_occ_out && n_occ > 0) {
+    if (n_tgt == 0)
+      return cuda_status(cudaMemsetAsync(grad_occ_out, 0, (size_t)p->nk * n_occ * p->npw_max * 16, s));
+    if (bad_ptr(c_occ) || bad_ptr(w_occ) || bad_ptr(c_tgt)) return XX_ERR_INVALID_ARGUMENT;
+    if ((st = run_vjp_occ(p, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, ybar, grad_occ_out, s)))
+      return st;
+  }
+  return XX_OK;
 }
 
 int xx_sync(xx_plan p, void* stream, double timeout_s) {

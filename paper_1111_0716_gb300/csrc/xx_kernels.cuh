@@ -618,6 +618,70 @@ __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_c(PairArgs p) {
   }
 }
 
+// Pass C with the roles swapped (vector-Jacobian product of V_x c with
+// respect to the occupied orbitals): grid (TJ, N); CTA (tj, z) owns occupied
+// band j and loops over the TA targets of the batch, accumulating
+// conj(W_aj) * f_a in registers (f = u_tgt grids: the cotangent's grids or the
+// targets' grids), then adds coef * w_j times the plane into the FP64
+// accumulator of j.
+template <int N, typename T>
+__global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_ct(PairArgs p) {
+  using C = cplx<T>;
+  using G = PlaneCfg<N, T>;
+  constexpr int A = G::A, B = G::B, NT = G::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* tw2 = tw + N;
+  C* s0 = tw2 + N;
+  C* s1 = s0 + G::BUF;
+  load_twiddles<N, T>(tw, p.tw);
+  __syncthreads();
+  make_twiddles2<N, T>(tw2, tw);
+  __syncthreads();
+  const int tj = blockIdx.x, z = blockIdx.y;
+  constexpr long long plane = (long long)N * N;
+  const int P1 = p.P1;
+  const long long pstride = (long long)p.P2 * p.P1;
+  C acc[G::X2_IT][B];
+#pragma unroll
+  for (int i = 0; i < G::X2_IT; ++i)
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) acc[i][k2] = czero<C>();
+#pragma unroll 1
+  for (int ta = 0; ta < p.TA; ++ta) {
+    const C* in = reinterpret_cast<const C*>(p.inter) + ((long long)(ta * p.TJ + tj) * N + z) * pstride;
+    const C* fa = reinterpret_cast<const C*>(p.u_tgt) + ta * p.u_tgt_stride + z * plane;
+    const C* next = ta + 1 < p.TA ? in + (long long)p.TJ * N * pstride : nullptr;
+    plane_inverse<N, T, false>(
+        tw, tw2, s0, s1, p.h1, p.P1, p.h2, [&](int kyb, int kxb) { return in[kyb * P1 + kxb]; },
+        [&](int i, int k2, int y, int x, C v) {
+          const C t = cmulc(v, fa[y * N + x]);   // conj(W) * f_a
+          acc[i][k2].x += t.x;
+          acc[i][k2].y += t.y;
+        },
+        fa, plane * (long long)sizeof(C), next, pstride * (long long)sizeof(C));
+  }
+  const double cf = p.coef * p.w_occ[tj];
+  double2* dst = p.acc + tj * plane * N + z * plane;
+#pragma unroll
+  for (int i = 0; i < G::X2_IT; ++i) {
+    const int it = threadIdx.x + i * NT;
+    if (it < N * A) {
+      int k1, row;
+      x2_item<A>(it, k1, row);
+      const int y = row / B + A * (row % B);
+#pragma unroll
+      for (int k2 = 0; k2 < B; ++k2) {
+        double2* o = dst + y * N + k1 + A * k2;
+        double2 cur = *o;
+        cur.x += cf * (double)acc[i][k2].x;
+        cur.y += cf * (double)acc[i][k2].y;
+        *o = cur;
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------ kernel table (a2) --
 
 // v(k - q + G)/N and dv/dmu/N^2 over the pruned box, evaluated in FP64.

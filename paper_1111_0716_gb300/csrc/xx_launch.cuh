@@ -14,6 +14,7 @@ struct KernelSet {
   void (*pass_b)(const PairArgs&, cudaStream_t);
   void (*pass_b_dmu)(const PairArgs&, cudaStream_t);
   void (*pass_c)(const PairArgs&, cudaStream_t);
+  void (*pass_ct)(const PairArgs&, cudaStream_t);
   void (*s2g_z)(const GridArgs&, cudaStream_t);
   void (*s2g_xy)(const GridArgs&, cudaStream_t);
 };
@@ -54,6 +55,12 @@ template <int N, typename T> void launch_pass_c(const PairArgs& p, cudaStream_t 
   allow_smem(k_pass_c<N, T>, sm);
   k_pass_c<N, T><<<dim3(p.TA, N), G::NT, sm, s>>>(p);
 }
+template <int N, typename T> void launch_pass_ct(const PairArgs& p, cudaStream_t s) {
+  using G = PlaneCfg<N, T>;
+  const size_t sm = G::smem();
+  allow_smem(k_pass_ct<N, T>, sm);
+  k_pass_ct<N, T><<<dim3(p.TJ, N), G::NT, sm, s>>>(p);
+}
 template <int N, typename T> void launch_s2g_z(const GridArgs& g, cudaStream_t s) {
   const size_t sm = smem_pencil<N, T>(g.Q1, 0);
   allow_smem(k_s2g_z<N, kThreads, T>, sm);
@@ -81,9 +88,11 @@ template <int N> const KernelTable* make_table() {
   static const KernelTable t = {
       N,
       {launch_pass_a<N, float>, launch_pass_b<N, float>, launch_pass_b_dmu<N, float>,
-       launch_pass_c<N, float>, launch_s2g_z<N, float>, launch_s2g_xy<N, float>},
+       launch_pass_c<N, float>, launch_pass_ct<N, float>, launch_s2g_z<N, float>,
+       launch_s2g_xy<N, float>},
       {launch_pass_a<N, double>, launch_pass_b<N, double>, launch_pass_b_dmu<N, double>,
-       launch_pass_c<N, double>, launch_s2g_z<N, double>, launch_s2g_xy<N, double>},
+       launch_pass_c<N, double>, launch_pass_ct<N, double>, launch_s2g_z<N, double>,
+       launch_s2g_xy<N, double>},
       launch_g2s_xy<N>,
       launch_g2s_z<N>};
   return &t;

@@ -37,7 +37,7 @@ EXPORTS = ("xx_create", "xx_destroy", "xx_apply", "xx_apply_range", "xx_energy",
            "xx_energy_range", "xx_energy_from_vx", "xx_energy_from_vx_range",
            "xx_apply_backward", "xx_sync", "xx_set_batch", "xx_profile_enable",
            "xx_profile_read", "xx_plan_info", "xx_status_string", "xx_energy_from_vx_noalloc",
-           "xx_run_many")
+           "xx_run_many", "xx_apply_vjp")
 
 PROF_CLASSES = ("pass_a", "pass_b", "pass_c", "sphere_to_grid", "grid_to_sphere",
                 "kernel_table", "reduce", "pass_b_dmu")
@@ -95,6 +95,7 @@ def load(path: Optional[str] = None):
     lib.xx_profile_read.argtypes = [P, P, P, I, I]
     lib.xx_energy_from_vx_noalloc.argtypes = [I, I, I, P, P, P, P, P, P]
     lib.xx_run_many.argtypes = [I, ctypes.POINTER(xx_job), P]
+    lib.xx_apply_vjp.argtypes = [P, P, I, P, I, P, I, P, P, P, P]
     lib.xx_status_string.argtypes = [I]
     lib.xx_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -203,6 +204,13 @@ def xx_apply_backward(plan, c, w, n_b, vx, grad_ex, dc_out, dmu_out, stream=None
     _check(load().xx_apply_backward(plan, _dptr(c), _dptr(w), int(n_b), _dptr(vx),
                                     float(grad_ex), _dptr(dc_out), _dptr(dmu_out),
                                     _stream_ptr(stream)), "xx_apply_backward")
+
+
+def xx_apply_vjp(plan, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, ybar, grad_tgt_out,
+                 grad_occ_out, stream=None):
+    _check(load().xx_apply_vjp(plan, _dptr(c_occ), int(ld_occ), _dptr(w_occ), int(n_occ),
+                               _dptr(c_tgt), int(n_tgt), _dptr(ybar), _dptr(grad_tgt_out),
+                               _dptr(grad_occ_out), _stream_ptr(stream)), "xx_apply_vjp")
 
 
 def xx_run_many(jobs, stream=None):
@@ -364,6 +372,16 @@ class Plan:
         xx_apply_backward(self.handle, c, w, n_b, vx, grad_ex, dc, dmu, stream)
         return dc, dmu
 
+    def vjp(self, c_occ, w_occ, c_tgt, ybar, want_tgt=True, want_occ=True, stream=None):
+        """(dL/dc_tgt*, dL/dc_occ*) for the cotangent ybar = dL/d(V_x c_tgt)*."""
+        import torch
+        gt = torch.empty_like(c_tgt) if want_tgt else None
+        go = torch.empty_like(c_occ) if want_occ else None
+        n_occ = c_occ.shape[1]
+        xx_apply_vjp(self.handle, c_occ, n_occ, w_occ, n_occ, c_tgt, c_tgt.shape[1], ybar, gt, go,
+                     stream)
+        return gt, go
+
     def sync(self, timeout_s: float = 0.0, stream=None):
         xx_sync(self.handle, stream, timeout_s)
 
@@ -404,6 +422,47 @@ def _exchange_function():
             return gc, None, gmu, None
 
     return ExchangeEnergy
+
+
+def _apply_function():
+    import torch
+
+    class ExchangeApply(torch.autograd.Function):
+        """y = V_x[c_occ] c_tgt with gradients for both orbital sets.
+
+        forward(c_occ, w_occ, c_tgt, plan) -> y.  torch's complex gradients are
+        2 dL/dz*: backward passes grad_y / 2 as the Wirtinger cotangent to
+        xx_apply_vjp and doubles the results.  Occupations get no gradient.
+        """
+
+        @staticmethod
+        def forward(ctx, c_occ, w_occ, c_tgt, plan):
+            c_occ, w_occ, c_tgt = c_occ.contiguous(), w_occ.contiguous(), c_tgt.contiguous()
+            ctx.plan = plan
+            ctx.save_for_backward(c_occ, w_occ, c_tgt)
+            return plan.apply(c_occ, w_occ, c_tgt)
+
+        @staticmethod
+        def backward(ctx, grad_y):
+            c_occ, w_occ, c_tgt = ctx.saved_tensors
+            ybar = (0.5 * grad_y).contiguous()
+            gt, go = ctx.plan.vjp(c_occ, w_occ, c_tgt, ybar, want_tgt=ctx.needs_input_grad[2],
+                                  want_occ=ctx.needs_input_grad[0])
+            return (2.0 * go if go is not None else None, None,
+                    2.0 * gt if gt is not None else None, None)
+
+    return ExchangeApply
+
+
+_EXA = None
+
+
+def exchange_apply(c_occ, w_occ, c_tgt, plan):
+    """Differentiable V_x[c_occ] c_tgt (see ExchangeApply)."""
+    global _EXA
+    if _EXA is None:
+        _EXA = _apply_function()
+    return _EXA.apply(c_occ, w_occ, c_tgt, plan)
 
 
 _EXF = None

@@ -1,0 +1,91 @@
+"""Vector-Jacobian product of V_x c (xx_apply_vjp) against finite differences of
+the FP64 oracle's forward application, and the autograd Function built on it.
+
+With L = Re <p|V_x[c_occ] c_tgt>, L is linear in c_tgt and quadratic
+(sesquilinear) in c_occ, so central differences are exact up to rounding."""
+import numpy as np
+import pytest
+
+from paper_1111_0716_gb300 import synth
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    return gu.need_gpu()
+
+
+def rhombo24(seed=21):
+    return synth.make_workload("rhombo24", synth.rhombohedral_lattice(7.5, 65.0), (24,) * 3,
+                               synth.monkhorst_pack(2), 2.4, 4, 6, [1.0, 1.0, 0.75, 0.3], seed)
+
+
+def masked_random(rng, wl, shape):
+    d = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    for k in range(wl.nk):
+        d[k, :, wl.npw[k]:] = 0
+    return d / np.linalg.norm(d)
+
+
+def gpu_vjp(xx, wl, ybar, prec):
+    plan = xx.Plan.from_workload(wl, precision=prec)
+    gt, go = plan.vjp(gu.dev(wl.c_occ), gu.dev(wl.w_occ), gu.dev(wl.c_tgt), gu.dev(ybar))
+    plan.sync(timeout_s=600.0)
+    out = gt.cpu().numpy(), go.cpu().numpy()
+    plan.close()
+    return out
+
+
+@pytest.mark.parametrize("make", [rhombo24, synth.tiny_cubic])
+def test_vjp_matches_finite_differences_of_oracle(gpu, oracle_mod, make):
+    torch, xx = gpu
+    wl = make()
+    rng = np.random.default_rng(3)
+    pvec = masked_random(rng, wl, wl.c_tgt.shape)
+    gt, go = gpu_vjp(xx, wl, 0.5 * pvec, 1)             # dL/dy* = p / 2
+
+    def loss(c_occ=None, c_tgt=None):
+        vx = oracle_mod.apply(wl, c_occ=c_occ, c_tgt=c_tgt)
+        return float(np.real(np.vdot(pvec, vx)))
+    h = 1e-3
+    for _ in range(4):
+        d = masked_random(rng, wl, wl.c_tgt.shape)
+        fd = (loss(c_tgt=wl.c_tgt + h * d) - loss(c_tgt=wl.c_tgt - h * d)) / (2 * h)
+        an = 2.0 * np.real(np.vdot(d, gt))
+        assert abs(fd - an) <= 1e-9 * max(abs(an), np.abs(gt).max())
+        d = masked_random(rng, wl, wl.c_occ.shape)
+        fd = (loss(c_occ=wl.c_occ + h * d) - loss(c_occ=wl.c_occ - h * d)) / (2 * h)
+        an = 2.0 * np.real(np.vdot(d, go))
+        assert abs(fd - an) <= 1e-9 * max(abs(an), np.abs(go).max())
+
+
+def test_vjp_mixed_precision_matches_fp64(gpu):
+    torch, xx = gpu
+    wl = rhombo24()
+    ybar = masked_random(np.random.default_rng(5), wl, wl.c_tgt.shape)
+    gt64, go64 = gpu_vjp(xx, wl, ybar, 1)
+    gt32, go32 = gpu_vjp(xx, wl, ybar, 0)
+    assert gu.rel_max(gt32, gt64) <= gu.FP32_TOL
+    assert gu.rel_max(go32, go64) <= gu.FP32_TOL
+
+
+def test_autograd_apply_function(gpu, oracle_mod):
+    torch, xx = gpu
+    wl = rhombo24()
+    plan = xx.Plan.from_workload(wl, precision=1)
+    rng = np.random.default_rng(11)
+    pvec = masked_random(rng, wl, wl.c_tgt.shape)
+    c_occ = gu.dev(wl.c_occ).requires_grad_(True)
+    c_tgt = gu.dev(wl.c_tgt).requires_grad_(True)
+    y = xx.exchange_apply(c_occ, gu.dev(wl.w_occ), c_tgt, plan)
+    ref = oracle_mod.apply(wl)
+    assert gu.rel_max(y.detach().cpu().numpy(), ref) <= gu.FP64_TOL
+    loss = torch.real(torch.sum(torch.conj(gu.dev(pvec)) * y))
+    loss.backward()
+    gt, go = gpu_vjp(xx, wl, 0.5 * pvec, 1)
+    # torch convention: .grad = 2 dL/dz*
+    assert gu.rel_max(c_tgt.grad.cpu().numpy(), 2 * gt) <= 1e-12
+    assert gu.rel_max(c_occ.grad.cpu().numpy(), 2 * go) <= 1e-12
+    plan.close()
