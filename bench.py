@@ -363,6 +363,8 @@ def main():
                        "nk": wl.nk, "n_occ": wl.n_occ, "n_tgt": wl.n_tgt,
                        "pairs_per_step": pairs, "precision": "FP32 FFTs and products, FP64 "
                        "accumulation, kernel table and reductions",
+                       "pairs_counted": "logical (k, a, q, j) applications; on the 8 diagonal "
+                       "k = q blocks each occupied pair is transformed once (W_ja = conj W_aj)",
                        "batch": [TA, TJ], "l2": "inputs larger than L2 (orbital grids %.1f GB)"
                        % (wl.nk * wl.n_tgt * 96 ** 3 * 8 / 1e9), "E_x": e_x},
             "e2e": {"value": world * pairs * e2e_steps / t_e2e, "unit": UNIT,

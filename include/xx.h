@@ -233,6 +233,15 @@ int xx_apply_vjp(xx_plan plan, const void *c_occ, int ld_occ, const double *w_oc
  */
 int xx_sync(xx_plan plan, void *stream, double timeout_s);
 
+/* Plan options for xx_set_option. */
+#define XX_OPT_PAIR_SYMMETRY 0  /* value != 0 (default): on diagonal blocks k = q, when the
+                                   occupied grids are the leading target grids, transform each
+                                   band pair once and use W_ja = conj(W_aj) for the other
+                                   target (the result differs only by rounding order) */
+
+/* Set a plan option; XX_ERR_INVALID_ARGUMENT for an unknown option. */
+int xx_set_option(xx_plan plan, int option, long long value);
+
 /* Override the band-pair batch shape (targets x occupied per batch); 0 keeps
  * the automatic choice.  Takes effect at the next call. */
 int xx_set_batch(xx_plan plan, int targets_per_batch, int occupied_per_batch);

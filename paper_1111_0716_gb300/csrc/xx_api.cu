@@ -193,6 +193,7 @@ struct xx_plan_s {
   int prec = 0;
   size_t cap = 0;
   int ta_user = 0, tj_user = 0;
+  bool pair_symmetry = true;
   int ta_last = 0, tj_last = 0;
   const KernelTable* kt = nullptr;
   int* d_miller = nullptr;   // [nk][npw_max][3]
@@ -483,12 +484,54 @@ int run_apply(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, const do
   if ((st = ensure(p, p->inter, (size_t)TA * TJ * p->N * P(p, 1) * P(p, 0) * eb))) return st;
   if ((st = ensure(p, p->acc, (size_t)n_tgt * n3(p) * 16))) return st;
   const KernelSet& ks = kset(p);
+  // k = q pair symmetry: with the occupied grids shared with the leading
+  // targets, W_ja = conj(W_aj) on the diagonal block (v(G) = v(-G) there), so the
+  // occupied square is tiled and only tiles I <= J are transformed.
+  const bool sym = shared && p->pair_symmetry && n_occ > 1;
+  const int T = TJ < TA ? TJ : TA;
   for (int kk = 0; kk < kn; ++kk) {
     const int k = k0 + kk;
     cudaMemsetAsync(p->acc.p, 0, (size_t)n_tgt * n3(p) * 16, s);
     for (int q = 0; q < p->nk; ++q) {
       if ((st = kernel_table_for(p, k, q, false, s))) return st;
-      for (int a0 = 0; a0 < n_tgt; a0 += TA) {
+      const bool diag = sym && q == k;
+      if (diag) {
+        for (int i0 = 0; i0 < n_occ; i0 += T) {
+          const int ti = (n_occ - i0) < T ? (n_occ - i0) : T;
+          for (int j0 = i0; j0 < n_occ; j0 += T) {
+            const int tj = (n_occ - j0) < T ? (n_occ - j0) : T;
+            PairArgs a = pair_args(p, ti, tj);
+            a.u_tgt = grid_ptr(p, true, kk, i0, n_occ, n_tgt);
+            a.u_occ = grid_ptr(p, true, q, j0, n_occ, n_tgt);
+            a.acc = (double2*)p->acc.p + (long long)i0 * n3(p);
+            a.w_occ = w_occ + (long long)q * n_occ + j0;
+            int e = prof_begin(p, s);
+            ks.pass_a(a, s);
+            prof_end(p, XX_PROF_PASS_A, e, s);
+            e = prof_begin(p, s);
+            ks.pass_b(a, s);
+            prof_end(p, XX_PROF_PASS_B, e, s);
+            e = prof_begin(p, s);
+            ks.pass_c(a, s);
+            prof_end(p, XX_PROF_PASS_C, e, s);
+            int nl = 3;
+            if (j0 > i0) {
+              // targets of tile J receive -(w_a/N_k) u_a conj(W_aj) from tile I
+              PairArgs c = a;
+              c.u_tgt = grid_ptr(p, true, kk, i0, n_occ, n_tgt);
+              c.w_tgt = w_occ + (long long)k * n_occ + i0;
+              c.w_occ = nullptr;
+              c.acc = (double2*)p->acc.p + (long long)j0 * n3(p);
+              e = prof_begin(p, s);
+              ks.pass_ct(c, s);
+              prof_end(p, XX_PROF_PASS_C, e, s);
+              ++nl;
+            }
+            if ((st = launched(p, nl))) return st;
+          }
+        }
+      }
+      for (int a0 = diag ? n_occ : 0; a0 < n_tgt; a0 += TA) {
         const int ta = (n_tgt - a0) < TA ? (n_tgt - a0) : TA;
         for (int j0 = 0; j0 < n_occ; j0 += TJ) {
           const int tj = (n_occ - j0) < TJ ? (n_occ - j0) : TJ;
@@ -973,6 +1016,17 @@ int xx_sync(xx_plan p, void* stream, double timeout_s) {
     return XX_ERR_DEVICE_FLAG;
   }
   return XX_OK;
+}
+
+int xx_set_option(xx_plan p, int option, long long value) {
+  if (!p) return XX_ERR_INVALID_ARGUMENT;
+  switch (option) {
+    case XX_OPT_PAIR_SYMMETRY:
+      p->pair_symmetry = value != 0;
+      return XX_OK;
+    default:
+      return XX_ERR_INVALID_ARGUMENT;
+  }
 }
 
 int xx_set_batch(xx_plan p, int targets_per_batch, int occupied_per_batch) {

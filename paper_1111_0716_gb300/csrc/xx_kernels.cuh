@@ -618,12 +618,13 @@ __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_c(PairArgs p) {
   }
 }
 
-// Pass C with the roles swapped (vector-Jacobian product of V_x c with
-// respect to the occupied orbitals): grid (TJ, N); CTA (tj, z) owns occupied
-// band j and loops over the TA targets of the batch, accumulating
-// conj(W_aj) * f_a in registers (f = u_tgt grids: the cotangent's grids or the
-// targets' grids), then adds coef * w_j times the plane into the FP64
-// accumulator of j.
+// Pass C with the roles swapped: grid (TJ, N); CTA (tj, z) owns band j of the
+// batch's second index and loops over the TA bands a of its first index,
+// accumulating w_a conj(W_aj) f_a in registers (f = u_tgt grids; w_a = w_tgt[a],
+// or 1 when w_tgt is null), then adds coef * w_occ[j] (or coef) times the plane
+// into the FP64 accumulator of j.  Uses: the vector-Jacobian product with
+// respect to the occupied orbitals (f = cotangent or target grids, weight
+// w_j), and the k = q pair symmetry W_ja = conj(W_aj) (f_a = u_a, weight w_a).
 template <int N, typename T>
 __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_ct(PairArgs p) {
   using C = cplx<T>;
@@ -652,16 +653,17 @@ __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_ct(PairArgs p) {
     const C* in = reinterpret_cast<const C*>(p.inter) + ((long long)(ta * p.TJ + tj) * N + z) * pstride;
     const C* fa = reinterpret_cast<const C*>(p.u_tgt) + ta * p.u_tgt_stride + z * plane;
     const C* next = ta + 1 < p.TA ? in + (long long)p.TJ * N * pstride : nullptr;
+    const T wa = p.w_tgt ? (T)p.w_tgt[ta] : (T)1;
     plane_inverse<N, T, false>(
         tw, tw2, s0, s1, p.h1, p.P1, p.h2, [&](int kyb, int kxb) { return in[kyb * P1 + kxb]; },
         [&](int i, int k2, int y, int x, C v) {
           const C t = cmulc(v, fa[y * N + x]);   // conj(W) * f_a
-          acc[i][k2].x += t.x;
-          acc[i][k2].y += t.y;
+          acc[i][k2].x += wa * t.x;
+          acc[i][k2].y += wa * t.y;
         },
         fa, plane * (long long)sizeof(C), next, pstride * (long long)sizeof(C));
   }
-  const double cf = p.coef * p.w_occ[tj];
+  const double cf = p.coef * (p.w_occ ? p.w_occ[tj] : 1.0);
   double2* dst = p.acc + tj * plane * N + z * plane;
 #pragma unroll
   for (int i = 0; i < G::X2_IT; ++i) {

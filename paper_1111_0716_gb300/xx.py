@@ -37,7 +37,8 @@ EXPORTS = ("xx_create", "xx_destroy", "xx_apply", "xx_apply_range", "xx_energy",
            "xx_energy_range", "xx_energy_from_vx", "xx_energy_from_vx_range",
            "xx_apply_backward", "xx_sync", "xx_set_batch", "xx_profile_enable",
            "xx_profile_read", "xx_plan_info", "xx_status_string", "xx_energy_from_vx_noalloc",
-           "xx_run_many", "xx_apply_vjp")
+           "xx_run_many", "xx_apply_vjp", "xx_set_option")
+XX_OPT_PAIR_SYMMETRY = 0
 
 PROF_CLASSES = ("pass_a", "pass_b", "pass_c", "sphere_to_grid", "grid_to_sphere",
                 "kernel_table", "reduce", "pass_b_dmu")
@@ -96,6 +97,7 @@ def load(path: Optional[str] = None):
     lib.xx_energy_from_vx_noalloc.argtypes = [I, I, I, P, P, P, P, P, P]
     lib.xx_run_many.argtypes = [I, ctypes.POINTER(xx_job), P]
     lib.xx_apply_vjp.argtypes = [P, P, I, P, I, P, I, P, P, P, P]
+    lib.xx_set_option.argtypes = [P, I, ctypes.c_longlong]
     lib.xx_status_string.argtypes = [I]
     lib.xx_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -238,6 +240,10 @@ def xx_sync(plan, stream=None, timeout_s: float = 0.0):
     _check(load().xx_sync(plan, _stream_ptr(stream), float(timeout_s)), "xx_sync")
 
 
+def xx_set_option(plan, option: int, value: int):
+    _check(load().xx_set_option(plan, int(option), int(value)), "xx_set_option")
+
+
 def xx_set_batch(plan, targets_per_batch: int, occupied_per_batch: int):
     _check(load().xx_set_batch(plan, int(targets_per_batch), int(occupied_per_batch)),
            "xx_set_batch")
@@ -304,6 +310,9 @@ class Plan:
 
     def profile_read(self, reset: bool = True) -> dict:
         return xx_profile_read(self.handle, reset)
+
+    def set_pair_symmetry(self, enable: bool):
+        xx_set_option(self.handle, XX_OPT_PAIR_SYMMETRY, 1 if enable else 0)
 
     def set_batch(self, targets: int, occupied: int):
         xx_set_batch(self.handle, targets, occupied)

@@ -205,3 +205,25 @@ def test_run_many_sweep_cells_match_single_runs(gpu):
         plan.close()
     with pytest.raises(xx.XXError):
         xx.xx_run_many([jobs[0], dict(jobs[0])])
+
+
+@pytest.mark.parametrize("make,prec,tol", [(synth.tiny_cubic, 1, 1e-12),
+                                           (synth.differentiation_cell, 0, gu.FP32_TOL),
+                                           (lambda: synth.sweep_cell(1), 1, 1e-12),
+                                           (lambda: rhombo24(), 1, 1e-12)])
+def test_pair_symmetry_matches_direct_pairs(gpu, make, prec, tol):
+    """k = q pair symmetry (default) against transforming every pair (option off)."""
+    torch, xx = gpu
+    wl = make()
+    out = []
+    for on in (True, False):
+        plan = xx.Plan.from_workload(wl, precision=prec)
+        plan.set_batch(3, 3)                     # several tiles, ragged edges
+        plan.set_pair_symmetry(on)
+        c = gu.dev(wl.c_tgt)
+        ex, vx = plan.energy(c, gu.dev(wl.w_occ), c, gu.dev(wl.w_tgt), shared=True)
+        plan.sync(timeout_s=600.0)
+        out.append((vx.cpu().numpy(), float(ex[0].item())))
+        plan.close()
+    assert gu.rel_max(out[0][0], out[1][0]) <= tol
+    assert abs(out[0][1] - out[1][1]) <= tol * abs(out[1][1])
