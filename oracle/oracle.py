@@ -9,6 +9,7 @@ its code.  Every function follows the steps of the paper's exchange loops
 from __future__ import annotations
 
 import ctypes
+import fcntl
 import os
 import subprocess
 
@@ -22,6 +23,15 @@ _lib = None
 
 def build_oracle(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2, OpenMP); returns the library path."""
+    with open(_LIB + ".lock", "w") as fh:
+        fcntl.flock(fh, fcntl.LOCK_EX)
+        try:
+            return _build_oracle(force)
+        finally:
+            fcntl.flock(fh, fcntl.LOCK_UN)
+
+
+def _build_oracle(force: bool) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".%d.tmp" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fopenmp", "-fPIC", "-shared",

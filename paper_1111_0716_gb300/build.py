@@ -7,6 +7,8 @@ next to this file.  Objects go to ``_build/`` (git-ignored).
 from __future__ import annotations
 
 import concurrent.futures as cf
+import contextlib
+import fcntl
 import glob
 import os
 import shutil
@@ -44,8 +46,25 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+@contextlib.contextmanager
+def _build_lock():
+    """Serialise concurrent builds (one process per GPU may call build())."""
+    os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as fh:
+        fcntl.flock(fh, fcntl.LOCK_EX)
+        try:
+            yield
+        finally:
+            fcntl.flock(fh, fcntl.LOCK_UN)
+
+
 def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
     """Compile (when stale) and return the path of libxx.so."""
+    with _build_lock():
+        return _build(force, verbose, jobs)
+
+
+def _build(force: bool, verbose: bool, jobs: int | None) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     headers = _headers()
