@@ -124,10 +124,11 @@ __global__ void __launch_bounds__(kRedThreads) k_energy(const double2* dots, con
   }
 }
 
-// acc[0] += sum over the batch's pairs of w_a w_j sum_kyb partial, one CTA, fixed order
+// acc[0] += scale * sum over the batch's pairs of w_a w_j sum_kyb partial, one CTA, fixed order
 __global__ void __launch_bounds__(kRedThreads) k_dmu_batch(const double* partial, int P2, int TA,
                                                            int TJ, const double* w_tgt,
-                                                           const double* w_occ, double* acc) {
+                                                           const double* w_occ, double scale,
+                                                           double* acc) {
   __shared__ double s_s[kRedThreads];
   double s = 0.0;
   for (int p = threadIdx.x; p < TA * TJ; p += kRedThreads) {
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dmu_batch(const double* partial
     if (threadIdx.x < off) s_s[threadIdx.x] += s_s[threadIdx.x + off];
     __syncthreads();
   }
-  if (threadIdx.x == 0) acc[0] += s_s[0];
+  if (threadIdx.x == 0) acc[0] += scale * s_s[0];
 }
 
 __global__ void k_scale_scalar(const double* in, double factor, double* out) {
@@ -586,13 +587,19 @@ int run_dmu(xx_plan p, const void* c, const double* w, int n_b, double grad, dou
   if ((st = ensure(p, p->dmu_acc, 8))) return st;
   cudaMemsetAsync(p->dmu_acc.p, 0, 8, s);
   const KernelSet& ks = kset(p);
+  // on diagonal blocks k = q, |rhohat_ja| = |rhohat_aj|: tiles I < J count twice,
+  // tiles J < I are skipped (square tiles, option XX_OPT_PAIR_SYMMETRY)
+  const int T = TJ < TA ? TJ : TA;
   for (int k = 0; k < p->nk; ++k)
     for (int q = 0; q < p->nk; ++q) {
       if ((st = kernel_table_for(p, k, q, true, s))) return st;
-      for (int a0 = 0; a0 < n_b; a0 += TA) {
-        const int ta = (n_b - a0) < TA ? (n_b - a0) : TA;
-        for (int j0 = 0; j0 < n_b; j0 += TJ) {
-          const int tj = (n_b - j0) < TJ ? (n_b - j0) : TJ;
+      const bool diag = p->pair_symmetry && q == k && n_b > 1;
+      const int SA = diag ? T : TA, SJ = diag ? T : TJ;
+      for (int a0 = 0; a0 < n_b; a0 += SA) {
+        const int ta = (n_b - a0) < SA ? (n_b - a0) : SA;
+        for (int j0 = diag ? a0 : 0; j0 < n_b; j0 += SJ) {
+          const int tj = (n_b - j0) < SJ ? (n_b - j0) : SJ;
+          const double scale = (diag && j0 > a0) ? 2.0 : 1.0;
           PairArgs a = pair_args(p, ta, tj);
           a.u_tgt = grid_ptr(p, true, k, a0, n_b, n_b);
           a.u_occ = grid_ptr(p, true, q, j0, n_b, n_b);
@@ -604,7 +611,8 @@ int run_dmu(xx_plan p, const void* c, const double* w, int n_b, double grad, dou
           prof_end(p, XX_PROF_PASS_B_DMU, e, s);
           k_dmu_batch<<<1, kRedThreads, 0, s>>>((const double*)p->partial.p, P(p, 1), ta, tj,
                                                 w + (long long)k * n_b + a0,
-                                                w + (long long)q * n_b + j0, (double*)p->dmu_acc.p);
+                                                w + (long long)q * n_b + j0, scale,
+                                                (double*)p->dmu_acc.p);
           if ((st = launched(p, 3))) return st;
         }
       }

@@ -122,3 +122,18 @@ def test_sync_time_limit_reports_timeout_without_cancelling(gpu):
     plan.sync(timeout_s=600.0)
     assert torch.isfinite(vx.abs()).all()
     plan.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, gu.FP32_TOL), (1, 1e-12)])
+def test_dmu_pair_symmetry_matches_direct_pairs(gpu, prec, tol):
+    torch, xx = gpu
+    wl = synth.sweep_cell(0)
+    out = []
+    for on in (True, False):
+        plan = xx.Plan.from_workload(wl, precision=prec)
+        plan.set_batch(5, 5)
+        plan.set_pair_symmetry(on)
+        _, dmu = plan.backward(gu.dev(wl.c_tgt), gu.dev(wl.w_tgt), grad_ex=1.0, want_dc=False)
+        out.append(float(dmu.item()))
+        plan.close()
+    assert abs(out[0] - out[1]) <= tol * abs(out[1])
