@@ -181,6 +181,23 @@ int xx_energy_from_vx_range(xx_plan plan, int k_first, int k_count, const void *
 int xx_apply_backward(xx_plan plan, const void *c, const double *w, int n_b, const void *vx,
                       double grad_ex, void *dc_out, double *dmu_out, void *stream);
 
+/*
+ * Strain derivative of E_x[c] (c both occupied and targets, as in
+ * xx_apply_backward): the analogue, for a cell without ions, of the paper's
+ * FOCK_FORCE derivative routine (Sec. "CPU Performance Analysis").  Under a
+ * homogeneous strain the lattice rows become a_i (I + eps) with the plane-wave
+ * coefficients held fixed, so g = (m + k - q).B becomes g (I - eps^T) and
+ * Omega becomes Omega det(I + eps):
+ *   dE_x/deps_ab = -delta_ab E_x
+ *                  + (s Omega / N_k^2) sum w_ka w_qj sum_G v'(|g|^2) g_a g_b |rhohat(G)|^2.
+ * (Stress = dE_x/deps / Omega in the convention sigma = (1/Omega) dE/deps.)
+ *   dex_deps: device double[9], row-major 3x3 (symmetric).
+ *   ex_out: device double[1] or NULL: E_x from the pair sum (Parseval form).
+ * Recomputes every codensity (forward transforms only).
+ */
+int xx_strain_derivative(xx_plan plan, const void *c, const double *w, int n_b, double *dex_deps,
+                         double *ex_out, void *stream);
+
 /* One independent exchange job for xx_run_many. */
 typedef struct {
   xx_plan plan;             /* each job needs its own plan (workspace) */

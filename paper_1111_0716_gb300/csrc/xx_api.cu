@@ -145,6 +145,38 @@ __global__ void __launch_bounds__(kRedThreads) k_dmu_batch(const double* partial
   if (threadIdx.x == 0) acc[0] += scale * s_s[0];
 }
 
+// acc[c] += scale * sum over the batch's pairs of w_a w_j sum_kyb partial[.][c], c < 7
+__global__ void __launch_bounds__(kRedThreads) k_strain_batch(const double* partial, int P2, int TA,
+                                                              int TJ, const double* w_tgt,
+                                                              const double* w_occ, double scale,
+                                                              double* acc) {
+  __shared__ double s_s[7][kRedThreads];
+  double s[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int p = threadIdx.x; p < TA * TJ; p += kRedThreads) {
+    const double w = w_tgt[p / TJ] * w_occ[p % TJ];
+    for (int r = 0; r < P2; ++r)
+      for (int c = 0; c < 7; ++c) s[c] += w * partial[((long long)p * P2 + r) * 7 + c];
+  }
+  for (int c = 0; c < 7; ++c) s_s[c][threadIdx.x] = s[c];
+  __syncthreads();
+  for (int off = kRedThreads / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off)
+      for (int c = 0; c < 7; ++c) s_s[c][threadIdx.x] += s_s[c][threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x < 7) acc[threadIdx.x] += scale * s_s[threadIdx.x][0];
+}
+
+// out[3a+b] = -delta_ab E_x + (s Omega / N_k^2) acc[comp(a,b)], E_x = -(s/2)(Omega/N_k^2) acc[0]
+__global__ void k_strain_final(const double* acc, double omega, int nk, double* out, double* ex) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double f = omega / ((double)nk * (double)nk);
+  const double e = -0.5 * kSpin * f * acc[0];
+  const int comp[9] = {1, 6, 5, 6, 2, 4, 5, 4, 3};
+  for (int i = 0; i < 9; ++i) out[i] = (i % 4 == 0 ? -e : 0.0) + kSpin * f * acc[comp[i]];
+  if (ex) ex[0] = e;
+}
+
 __global__ void k_scale_scalar(const double* in, double factor, double* out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = factor * in[0];
 }
@@ -183,6 +215,7 @@ struct xx_plan_s {
   int nk = 0;
   int npw_max = 0;
   double lattice[9];
+  double B[9];            // reciprocal rows
   double M[9];            // reciprocal metric
   double omega = 0.0;
   std::vector<double> kfrac;
@@ -202,7 +235,8 @@ struct xx_plan_s {
   void* d_tw32 = nullptr;
   void* d_tw64 = nullptr;
   int* d_err = nullptr;
-  DevBuf u_tgt, u_occ, inter, acc, vt, dvt, box, stage, dots, partial, dmu_acc, vx_tmp, u_bar;
+  DevBuf u_tgt, u_occ, inter, acc, vt, dvt, box, stage, dots, partial, dmu_acc, vx_tmp, u_bar,
+      stab;
   size_t ws_bytes = 0, peak_bytes = 0;
   long long launches = 0;
   // optional per-kernel-class timing with events on the launch stream
@@ -622,6 +656,70 @@ int run_dmu(xx_plan p, const void* c, const double* w, int n_b, double grad, dou
   return launched(p, 1);
 }
 
+// Strain derivative of E_x[c] at fixed coefficients: pass A + forward z with the
+// seven tables of k_strain_tab, reduced with w_a w_j (pair symmetry on k = q).
+int run_strain(xx_plan p, const void* c, const double* w, int n_b, double* out9, double* ex_out,
+               cudaStream_t s) {
+  int st = build_grids(p, 0, p->nk, c, n_b, n_b, c, n_b, true, s);
+  if (st) return st;
+  int TA, TJ;
+  batch_shape(p, n_b, n_b, &TA, &TJ);
+  const size_t eb = elem_bytes(p);
+  const long long nbox = (long long)P(p, 0) * P(p, 1) * P(p, 2);
+  if ((st = ensure(p, p->inter, (size_t)TA * TJ * p->N * P(p, 1) * P(p, 0) * eb))) return st;
+  if ((st = ensure(p, p->partial, (size_t)TA * TJ * P(p, 1) * 7 * 8))) return st;
+  if ((st = ensure(p, p->stab, (size_t)7 * nbox * (p->prec == XX_FP64 ? 8 : 4)))) return st;
+  if ((st = ensure(p, p->dmu_acc, 7 * 8))) return st;
+  cudaMemsetAsync(p->dmu_acc.p, 0, 7 * 8, s);
+  const KernelSet& ks = kset(p);
+  const int T = TJ < TA ? TJ : TA;
+  for (int k = 0; k < p->nk; ++k)
+    for (int q = 0; q < p->nk; ++q) {
+      VtabArgs va{};
+      std::memcpy(va.Bm, p->B, sizeof(va.Bm));
+      std::memcpy(va.M, p->M, sizeof(va.M));
+      for (int i = 0; i < 3; ++i) va.d[i] = p->kfrac[3 * k + i] - p->kfrac[3 * q + i];
+      va.h1 = p->h[0];
+      va.h2 = p->h[1];
+      va.h3 = p->h[2];
+      va.P1 = P(p, 0);
+      va.P2 = P(p, 1);
+      va.P3 = P(p, 2);
+      va.kernel = p->kernel;
+      va.mu = p->mu;
+      va.inv_n = 1.0 / (double)n3(p);
+      va.inv_n2 = va.inv_n * va.inv_n;
+      const int blocks = (int)((nbox + 255) / 256);
+      if (p->prec == XX_FP64)
+        k_strain_tab<double><<<blocks, 256, 0, s>>>((double*)p->stab.p, va);
+      else
+        k_strain_tab<float><<<blocks, 256, 0, s>>>((float*)p->stab.p, va);
+      if ((st = launched(p, 1))) return st;
+      const bool diag = p->pair_symmetry && q == k && n_b > 1;
+      const int SA = diag ? T : TA, SJ = diag ? T : TJ;
+      for (int a0 = 0; a0 < n_b; a0 += SA) {
+        const int ta = (n_b - a0) < SA ? (n_b - a0) : SA;
+        for (int j0 = diag ? a0 : 0; j0 < n_b; j0 += SJ) {
+          const int tj = (n_b - j0) < SJ ? (n_b - j0) : SJ;
+          const double scale = (diag && j0 > a0) ? 2.0 : 1.0;
+          PairArgs a = pair_args(p, ta, tj);
+          a.u_tgt = grid_ptr(p, true, k, a0, n_b, n_b);
+          a.u_occ = grid_ptr(p, true, q, j0, n_b, n_b);
+          a.dvt = p->stab.p;
+          ks.pass_a(a, s);
+          ks.pass_b_strain(a, s);
+          k_strain_batch<<<1, kRedThreads, 0, s>>>((const double*)p->partial.p, P(p, 1), ta, tj,
+                                                   w + (long long)k * n_b + a0,
+                                                   w + (long long)q * n_b + j0, scale,
+                                                   (double*)p->dmu_acc.p);
+          if ((st = launched(p, 3))) return st;
+        }
+      }
+    }
+  k_strain_final<<<1, 32, 0, s>>>((const double*)p->dmu_acc.p, p->omega, p->nk, out9, ex_out);
+  return launched(p, 1);
+}
+
 // Occupied-orbital part of the vector-Jacobian product of y = V_x[c_occ] c_tgt
 // for a cotangent ybar = dL/dy* (Wirtinger):
 //   dL/dc_qj* = P_q[ -(w_qj/N_k) sum_{k,a} ( ubar_ka conj(W_aj) + u_ka conj(Wbar_aj) ) ]
@@ -768,6 +866,7 @@ int xx_create(xx_plan* out, const double* lattice, const int* grid, int nk, cons
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j)
       p->M[3 * i + j] = B[3 * i] * B[3 * j] + B[3 * i + 1] * B[3 * j + 1] + B[3 * i + 2] * B[3 * j + 2];
+  std::memcpy(p->B, B, sizeof(p->B));
   p->kfrac.assign(kfrac, kfrac + 3 * nk);
   p->npw.assign(npw, npw + nk);
   for (int ax = 0; ax < 3; ++ax) {
@@ -813,7 +912,8 @@ int xx_destroy(xx_plan p) {
   if (!p) return XX_OK;
   cudaDeviceSynchronize();
   DevBuf* bufs[] = {&p->u_tgt, &p->u_occ, &p->inter, &p->acc, &p->vt, &p->dvt, &p->box,
-                    &p->stage, &p->dots, &p->partial, &p->dmu_acc, &p->vx_tmp, &p->u_bar};
+                    &p->stage, &p->dots, &p->partial, &p->dmu_acc, &p->vx_tmp, &p->u_bar,
+                    &p->stab};
   for (DevBuf* b : bufs) release(*b);
   if (p->d_miller) cudaFree(p->d_miller);
   if (p->d_npw) cudaFree(p->d_npw);
@@ -915,6 +1015,19 @@ int xx_apply_backward(xx_plan p, const void* c, const double* w, int n_b, const 
   }
   if (dmu_out) return run_dmu(p, c, w, n_b, grad_ex, dmu_out, s);
   return XX_OK;
+}
+
+int xx_strain_derivative(xx_plan p, const void* c, const double* w, int n_b, double* dex_deps,
+                         double* ex_out, void* stream) {
+  if (!p || n_b < 0 || bad_ptr(dex_deps)) return XX_ERR_INVALID_ARGUMENT;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_b == 0) {
+    cudaError_t e = cudaMemsetAsync(dex_deps, 0, 9 * sizeof(double), s);
+    if (e == cudaSuccess && ex_out) e = cudaMemsetAsync(ex_out, 0, sizeof(double), s);
+    return cuda_status(e);
+  }
+  if (bad_ptr(c) || bad_ptr(w)) return XX_ERR_INVALID_ARGUMENT;
+  return run_strain(p, c, w, n_b, dex_deps, ex_out, s);
 }
 
 int xx_run_many(int n_jobs, const xx_job* jobs, void* stream) {

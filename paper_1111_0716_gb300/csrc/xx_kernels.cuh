@@ -58,6 +58,7 @@ struct GridArgs {        // sphere <-> grid
 };
 
 struct VtabArgs {
+  double Bm[9];          // reciprocal rows b_i (Cartesian), for the strain tables
   double M[9];           // reciprocal metric b_i . b_j
   double d[3];           // k - q (fractional)
   int h1, h2, h3, P1, P2, P3;
@@ -713,6 +714,99 @@ __global__ void k_vtab(T* vt, T* dvt, VtabArgs a) {
     vt[i] = (T)(v * a.inv_n);
     if (dvt) dvt[i] = (T)(dv * a.inv_n2);
   }
+}
+
+// dv/dx for x = |g|^2: screened t = x/(4 mu^2), v'(x) = (4 pi/x^2)(t e^-t + expm1(-t)),
+// with the series sum_{m>=2} (-1)^(m-1) (m-1) t^m / m! for small t (the two
+// terms cancel there); Coulomb -4 pi/x^2.  The g = 0 point never contributes
+// (it is multiplied by g_a g_b = 0), so it returns 0.
+__device__ __forceinline__ double dv_dx(int kernel, double mu, double x, bool zero) {
+  const double pi = 3.14159265358979323846;
+  if (zero) return 0.0;
+  if (kernel != 0) return -4.0 * pi / (x * x);
+  const double t = x / (4.0 * mu * mu);
+  double f;
+  if (t < 0.05) {
+    double term = t;            // t^m / m! built up from m = 1
+    f = 0.0;
+    for (int m = 2; m <= 14; ++m) {
+      term *= t / m;
+      f += ((m & 1) ? 1.0 : -1.0) * (m - 1) * term;
+    }
+  } else {
+    f = t * exp(-t) + expm1(-t);
+  }
+  return 4.0 * pi / (x * x) * f;
+}
+
+// Seven tables over the pruned box for the strain derivative, FP64-evaluated:
+// tab[0] = v/N^2, tab[1..6] = v'(|g|^2) g_a g_b / N^2 for ab = xx, yy, zz, yz, xz, xy.
+template <typename T>
+__global__ void k_strain_tab(T* tab, VtabArgs a) {
+  const long long n = (long long)a.P1 * a.P2 * a.P3;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % a.P1), ky = (int)((i / a.P1) % a.P2), kz = (int)(i / ((long long)a.P1 * a.P2));
+    const double m0 = (double)(kx - a.h1) + a.d[0];
+    const double m1 = (double)(ky - a.h2) + a.d[1];
+    const double m2 = (double)(kz - a.h3) + a.d[2];
+    const bool zero = (m0 == 0.0 && m1 == 0.0 && m2 == 0.0);
+    double g[3];
+    for (int c = 0; c < 3; ++c) g[c] = m0 * a.Bm[c] + m1 * a.Bm[3 + c] + m2 * a.Bm[6 + c];
+    const double x = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    const double pi = 3.14159265358979323846;
+    double v;
+    if (a.kernel == 0)
+      v = zero ? pi / (a.mu * a.mu) : 4.0 * pi / x * (-expm1(-x / (4.0 * a.mu * a.mu)));
+    else
+      v = zero ? 0.0 : 4.0 * pi / x;
+    const double dv = dv_dx(a.kernel, a.mu, x, zero) * a.inv_n2;
+    tab[i] = (T)(v * a.inv_n2);
+    tab[n + i] = (T)(dv * g[0] * g[0]);
+    tab[2 * n + i] = (T)(dv * g[1] * g[1]);
+    tab[3 * n + i] = (T)(dv * g[2] * g[2]);
+    tab[4 * n + i] = (T)(dv * g[1] * g[2]);
+    tab[5 * n + i] = (T)(dv * g[0] * g[2]);
+    tab[6 * n + i] = (T)(dv * g[0] * g[1]);
+  }
+}
+
+// Pass B for the strain derivative: forward z only, partial[pair][kyb][c] =
+// sum tab_c |rho|^2 for the seven tables (p.dvt holds them, P3*P2*P1 apart).
+template <int N, int NT, typename T>
+__global__ void __launch_bounds__(NT) k_pass_b_strain(PairArgs p) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* sZ = tw + N;
+  __shared__ double red[7][NT];
+  load_twiddles<N, T>(tw, p.tw);
+  __syncthreads();
+  const int kyb = blockIdx.x, pair = blockIdx.y;
+  const int P1 = p.P1, P2 = p.P2;
+  const long long zstride = (long long)P2 * P1;
+  const long long nbox = zstride * p.P3;
+  const C* row = reinterpret_cast<const C*>(p.inter) + (long long)pair * N * zstride + (long long)kyb * P1;
+  const T* tab = reinterpret_cast<const T*>(p.dvt);
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  pencil_forward<N, NT, T>(
+      tw, sZ, P1, p.h3, [&](int z, int c) { return row[z * zstride + c]; },
+      [&](int kzb, int c, C v) {
+        const long long i = ((long long)kzb * P2 + kyb) * P1 + c;
+        const double r2 = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+#pragma unroll
+        for (int t = 0; t < 7; ++t) acc[t] += (double)tab[t * nbox + i] * r2;
+      });
+#pragma unroll
+  for (int t = 0; t < 7; ++t) red[t][threadIdx.x] = acc[t];
+  __syncthreads();
+  for (int off = NT / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off)
+#pragma unroll
+      for (int t = 0; t < 7; ++t) red[t][threadIdx.x] += red[t][threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x < 7) p.partial[((long long)pair * P2 + kyb) * 7 + threadIdx.x] = red[threadIdx.x][0];
 }
 
 // ---------------------------------------------------- sphere <-> grid (a1, a8) --

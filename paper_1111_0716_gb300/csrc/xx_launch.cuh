@@ -13,6 +13,7 @@ struct KernelSet {
   void (*pass_a)(const PairArgs&, cudaStream_t);
   void (*pass_b)(const PairArgs&, cudaStream_t);
   void (*pass_b_dmu)(const PairArgs&, cudaStream_t);
+  void (*pass_b_strain)(const PairArgs&, cudaStream_t);
   void (*pass_c)(const PairArgs&, cudaStream_t);
   void (*pass_ct)(const PairArgs&, cudaStream_t);
   void (*s2g_z)(const GridArgs&, cudaStream_t);
@@ -48,6 +49,11 @@ template <int N, typename T> void launch_pass_b_dmu(const PairArgs& p, cudaStrea
   const size_t sm = smem_pencil<N, T>(p.P1, 0);
   allow_smem(k_pass_b_dmu<N, kThreads, T>, sm);
   k_pass_b_dmu<N, kThreads, T><<<dim3(p.P2, p.TA * p.TJ), kThreads, sm, s>>>(p);
+}
+template <int N, typename T> void launch_pass_b_strain(const PairArgs& p, cudaStream_t s) {
+  const size_t sm = smem_pencil<N, T>(p.P1, 0);
+  allow_smem(k_pass_b_strain<N, kThreads, T>, sm);
+  k_pass_b_strain<N, kThreads, T><<<dim3(p.P2, p.TA * p.TJ), kThreads, sm, s>>>(p);
 }
 template <int N, typename T> void launch_pass_c(const PairArgs& p, cudaStream_t s) {
   using G = PlaneCfg<N, T>;
@@ -88,10 +94,10 @@ template <int N> const KernelTable* make_table() {
   static const KernelTable t = {
       N,
       {launch_pass_a<N, float>, launch_pass_b<N, float>, launch_pass_b_dmu<N, float>,
-       launch_pass_c<N, float>, launch_pass_ct<N, float>, launch_s2g_z<N, float>,
+       launch_pass_b_strain<N, float>, launch_pass_c<N, float>, launch_pass_ct<N, float>, launch_s2g_z<N, float>,
        launch_s2g_xy<N, float>},
       {launch_pass_a<N, double>, launch_pass_b<N, double>, launch_pass_b_dmu<N, double>,
-       launch_pass_c<N, double>, launch_pass_ct<N, double>, launch_s2g_z<N, double>,
+       launch_pass_b_strain<N, double>, launch_pass_c<N, double>, launch_pass_ct<N, double>, launch_s2g_z<N, double>,
        launch_s2g_xy<N, double>},
       launch_g2s_xy<N>,
       launch_g2s_z<N>};

@@ -37,7 +37,7 @@ EXPORTS = ("xx_create", "xx_destroy", "xx_apply", "xx_apply_range", "xx_energy",
            "xx_energy_range", "xx_energy_from_vx", "xx_energy_from_vx_range",
            "xx_apply_backward", "xx_sync", "xx_set_batch", "xx_profile_enable",
            "xx_profile_read", "xx_plan_info", "xx_status_string", "xx_energy_from_vx_noalloc",
-           "xx_run_many", "xx_apply_vjp", "xx_set_option")
+           "xx_run_many", "xx_apply_vjp", "xx_set_option", "xx_strain_derivative")
 XX_OPT_PAIR_SYMMETRY = 0
 
 PROF_CLASSES = ("pass_a", "pass_b", "pass_c", "sphere_to_grid", "grid_to_sphere",
@@ -98,6 +98,7 @@ def load(path: Optional[str] = None):
     lib.xx_run_many.argtypes = [I, ctypes.POINTER(xx_job), P]
     lib.xx_apply_vjp.argtypes = [P, P, I, P, I, P, I, P, P, P, P]
     lib.xx_set_option.argtypes = [P, I, ctypes.c_longlong]
+    lib.xx_strain_derivative.argtypes = [P, P, P, I, P, P, P]
     lib.xx_status_string.argtypes = [I]
     lib.xx_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -238,6 +239,11 @@ def xx_run_many(jobs, stream=None):
 
 def xx_sync(plan, stream=None, timeout_s: float = 0.0):
     _check(load().xx_sync(plan, _stream_ptr(stream), float(timeout_s)), "xx_sync")
+
+
+def xx_strain_derivative(plan, c, w, n_b, dex_deps, ex_out=None, stream=None):
+    _check(load().xx_strain_derivative(plan, _dptr(c), _dptr(w), int(n_b), _dptr(dex_deps),
+                                       _dptr(ex_out), _stream_ptr(stream)), "xx_strain_derivative")
 
 
 def xx_set_option(plan, option: int, value: int):
@@ -390,6 +396,14 @@ class Plan:
         xx_apply_vjp(self.handle, c_occ, n_occ, w_occ, n_occ, c_tgt, c_tgt.shape[1], ybar, gt, go,
                      stream)
         return gt, go
+
+    def strain_derivative(self, c, w, stream=None):
+        """(dE_x/deps as a device 3x3 float64, E_x) for orbitals c that are occupied and targets."""
+        import torch
+        d = torch.empty(9, dtype=torch.float64, device=c.device)
+        e = torch.empty(1, dtype=torch.float64, device=c.device)
+        xx_strain_derivative(self.handle, c, w, c.shape[1], d, e, stream)
+        return d.reshape(3, 3), e
 
     def sync(self, timeout_s: float = 0.0, stream=None):
         xx_sync(self.handle, stream, timeout_s)
