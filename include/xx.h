@@ -99,8 +99,10 @@ typedef struct {
  * miller[nk*npw_max*3] are HOST arrays, copied into the plan.  kernel_type is
  * XX_KERNEL_HSE (mu > 0, bohr^-1) or XX_KERNEL_COULOMB_G0_DROPPED (mu
  * ignored).  precision is XX_FP32_MIXED or XX_FP64.  workspace_cap bounds the
- * band-pair intermediate in bytes (0 = 2 GiB); it sets how many band pairs are
- * processed per batch (the paper's NSIM control of GPU memory).
+ * band-pair intermediate in bytes (0 = 16 GiB); it sets how many band pairs are
+ * processed per batch (the paper's NSIM control of GPU memory): the default
+ * batch of 64 targets x 80 occupied bands is halved (occupied first) until its
+ * intermediate fits.
  * Returns XX_ERR_INVALID_ARGUMENT, XX_ERR_UNSUPPORTED_GRID, XX_ERR_GRID_ALIASING,
  * XX_ERR_NO_DEVICE, XX_ERR_OUT_OF_MEMORY or XX_OK; *out is NULL on failure.
  */

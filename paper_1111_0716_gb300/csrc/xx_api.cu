@@ -252,7 +252,7 @@ struct xx_plan_s {
 
 namespace {
 
-const size_t kDefaultCap = (size_t)2 << 30;
+const size_t kDefaultCap = (size_t)16 << 30;
 const int kGridChunk = 32;   // orbitals per sphere<->grid launch
 
 int cuda_status(cudaError_t e) {
@@ -444,8 +444,11 @@ int kernel_table_for(xx_plan p, int k, int q, bool with_dmu, cudaStream_t s) {
 
 void batch_shape(xx_plan p, int n_tgt, int n_occ, int* TA, int* TJ) {
   const size_t per_pair = (size_t)p->N * P(p, 1) * P(p, 0) * elem_bytes(p);
-  int ta = p->ta_user > 0 ? p->ta_user : 32;
-  int tj = p->tj_user > 0 ? p->tj_user : 16;
+  // 64 x 80 measured best on the 96^3 workload: a long occupied loop amortises
+  // pass C's prologue and FP64 accumulator update, and 6144 CTAs per launch
+  // keep the last wave short
+  int ta = p->ta_user > 0 ? p->ta_user : 64;
+  int tj = p->tj_user > 0 ? p->tj_user : 80;
   if (ta > n_tgt) ta = n_tgt;
   if (tj > n_occ) tj = n_occ;
   while ((size_t)ta * tj * per_pair > p->cap && tj > 1) tj = (tj + 1) / 2;

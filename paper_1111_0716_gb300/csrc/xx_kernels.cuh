@@ -511,13 +511,13 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_pass_b(PairArgs 
   __syncthreads();
   const int kyb = blockIdx.x, pair = blockIdx.y;
   const int P1 = p.P1, P2 = p.P2;
-  const long long zstride = (long long)P2 * P1;
-  C* row = reinterpret_cast<C*>(p.inter) + (long long)pair * N * zstride + (long long)kyb * P1;
-  const T* vt = reinterpret_cast<const T*>(p.vt);
+  const int zstride = P2 * P1;                 // a pair's planes stay within 32-bit offsets
+  C* row = reinterpret_cast<C*>(p.inter) + (long long)pair * N * zstride + kyb * P1;
+  const T* vt = reinterpret_cast<const T*>(p.vt) + kyb * P1;
   pencil_forward<N, NT, T>(
       tw, sZ, P1, p.h3, [&](int z, int c) { return row[z * zstride + c]; },
       [&](int kzb, int c, C v) {
-        const T s = vt[((long long)kzb * P2 + kyb) * P1 + c];
+        const T s = vt[kzb * zstride + c];
         sK[kzb * P1 + c] = s * v;
       });
   __syncthreads();
