@@ -182,8 +182,8 @@ def reference_arm(args, rank, world):
 
 
 def profile_case(args):
-    """beta-boron 96^3, target k=0, 32 targets x 32 occupied bands x 8 q (8192 pairs),
-    in the benchmark's batch shape (32 targets x 16 occupied per launch)."""
+    """beta-boron 96^3, target k=0, 64 targets x 80 occupied bands x 8 q (40960 pairs),
+    in the benchmark's batch shape (64 targets x 80 occupied per launch)."""
     import torch
 
     import __graft_entry__
@@ -192,7 +192,7 @@ def profile_case(args):
     wl = synth.beta_boron()
     prec = xx.XX_FP64 if args.precision == "fp64" else xx.XX_FP32_MIXED
     plan = xx.Plan.from_workload(wl, precision=prec)
-    nt, no = 32, 32
+    nt, no = (16, 16) if args.profile_small else (64, 80)
     co = torch.from_numpy(wl.c_occ[:, :no].copy()).cuda()
     wo = torch.from_numpy(wl.w_occ[:, :no].copy()).cuda()
     ct = torch.from_numpy(wl.c_tgt[:1, :nt].copy()).cuda()
@@ -221,6 +221,9 @@ def main():
                          "bands, all q) once and exit: the case ncu captures")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="precision of --profile-case")
+    ap.add_argument("--profile-small", action="store_true",
+                    help="with --profile-case: 16 targets x 16 occupied bands (a few GB on the "
+                         "device, for multi-pass ncu captures)")
     ap.add_argument("--with-vjp", action="store_true",
                     help="also time the vector-Jacobian product (xx_apply_vjp, both orbital "
                          "sets) on 16 target bands of every k-point")

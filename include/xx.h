@@ -33,9 +33,9 @@
  * The library returns pure exchange: a hybrid functional's mixing fraction is
  * the caller's to apply.
  *
- * Grids: every axis must hold the codensity without wrap-around, i.e.
+ * Grids: every axis must hold the codensity without aliasing, i.e.
  * N_i >= 4 n_i + 1 where n_i is the largest |Miller index| along axis i over
- * all basis sets (the paper's "FFTs performed without wrap-around errors");
+ * all basis sets (the paper sizes its FFT grids so that no aliasing occurs);
  * otherwise xx_create returns XX_ERR_GRID_ALIASING.  Supported axis lengths:
  * 24, 32, 40, 48, 60, 64, 72, 80, 96, equal on all three axes.
  *
@@ -115,7 +115,10 @@ int xx_create(xx_plan *out, const double *lattice, const int *grid, int nk, cons
 int xx_destroy(xx_plan plan);
 
 /*
- * vx_out[k][a][g] = (V_x c_tgt)_ka(G) for every k and target a.
+ * vx_out[k][a][g] = (V_x c_tgt)_ka(G) for every k and target a: the operator
+ * the paper's FOCK_ACC applies (Sec. "CPU Performance Analysis"), evaluated by
+ * the k, q, band, band loops of Sec. "Our Implementation" (Eq. 2) as stated at
+ * the top of this file.
  *   c_occ: device complex128 [nk][ld_occ][npw_max]; the occupied orbitals are
  *          bands 0..n_occ-1 of each k (ld_occ >= n_occ band slots per k; 0
  *          means n_occ).  When c_occ == c_tgt and ld_occ == n_tgt the
@@ -140,8 +143,9 @@ int xx_apply_range(xx_plan plan, int k_first, int k_count, const void *c_occ, in
                    void *stream);
 
 /*
- * E_x of the targets: runs xx_apply into vx_out (device, required) and then
- * the deterministic FP64 reduction of (s/2)(1/N_k) sum w_tgt <c_tgt|V_x c_tgt>.
+ * E_x of the targets (Eq. 2, with the sign and spin readings stated at the top
+ * of this file): runs xx_apply into vx_out (device, required) and then the
+ * deterministic FP64 reduction of (s/2)(1/N_k) sum w_tgt <c_tgt|V_x c_tgt>.
  *   w_tgt: device double [nk][n_tgt].
  *   ex_out: device double[2] = {Re E_x, Im E_x}; the imaginary part is a
  *          diagnostic that vanishes for a Hermitian V_x.
@@ -167,7 +171,8 @@ int xx_energy_from_vx_range(xx_plan plan, int k_first, int k_count, const void *
                             void *stream);
 
 /*
- * Gradients of E_x[c] where the same orbitals c (device complex128
+ * Gradients of E_x[c] (the paper computes none; these are derivatives of Eq. 2)
+ * where the same orbitals c (device complex128
  * [nk][n_b][npw_max]) with occupations w (device double [nk][n_b]) are both the
  * occupied set and the targets.
  *   vx: V_x c from a previous xx_apply/xx_energy with these inputs (device), or
@@ -225,7 +230,8 @@ typedef struct {
 int xx_run_many(int n_jobs, const xx_job *jobs, void *stream);
 
 /*
- * Vector-Jacobian product of y = V_x[c_occ] c_tgt (xx_apply's output) for a
+ * Vector-Jacobian product (the paper has none; the derivative of the Eq. 2
+ * loops' output) of y = V_x[c_occ] c_tgt (xx_apply's output) for a
  * real loss L with cotangent ybar = dL/dy* (Wirtinger; device complex128
  * [nk][n_tgt][npw_max]).  Inputs as xx_apply.
  *   grad_tgt_out (device complex128 [nk][n_tgt][npw_max], or NULL):
