@@ -263,6 +263,20 @@ int xx_sync(xx_plan plan, void *stream, double timeout_s);
                                    occupied grids are the leading target grids, transform each
                                    band pair once and use W_ja = conj(W_aj) for the other
                                    target (the result differs only by rounding order) */
+#define XX_OPT_REAL_GAMMA 1     /* value != 0: the orbitals passed to later calls are real in
+                                   real space (c(-G) = conj c(G) for every G of the basis), so
+                                   every codensity is real and, at k = q = Gamma, so is every
+                                   W_aj.  Two occupied bands then share one transform: the
+                                   codensity of u_2p - i u_2p+1 with u_a is rho_a,2p +
+                                   i rho_a,2p+1, and the real and imaginary parts of its W are
+                                   the two bands' potentials.  Halves the transforms of
+                                   xx_apply, xx_energy, xx_apply_backward and
+                                   xx_strain_derivative (with XX_OPT_PAIR_SYMMETRY as well,
+                                   the k = q square is halved again); xx_apply_vjp keeps the
+                                   general path.  Allowed only on a plan with one k-point at
+                                   Gamma whose basis holds -G for every G (else
+                                   XX_ERR_INVALID_ARGUMENT); with complex orbitals the results
+                                   are wrong.  Default 0. */
 
 /* Set a plan option; XX_ERR_INVALID_ARGUMENT for an unknown option. */
 int xx_set_option(xx_plan plan, int option, long long value);

@@ -9,6 +9,7 @@
 //     for q: kernel table v(k - q + G)
 //       for each (target batch, occupied batch): pass A, pass B, pass C
 //     grid -> sphere of the accumulators into V_x c
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dmu_batch(const double* partial
   for (int p = threadIdx.x; p < TA * TJ; p += kRedThreads) {
     double t = 0.0;
     for (int r = 0; r < P2; ++r) t += partial[(long long)p * P2 + r];
-    s += w_tgt[p / TJ] * w_occ[p % TJ] * t;
+    s += w_tgt[p / TJ] * (w_occ ? w_occ[p % TJ] : 1.0) * t;
   }
   s_s[threadIdx.x] = s;
   __syncthreads();
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(kRedThreads) k_strain_batch(const double* part
   __shared__ double s_s[7][kRedThreads];
   double s[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int p = threadIdx.x; p < TA * TJ; p += kRedThreads) {
-    const double w = w_tgt[p / TJ] * w_occ[p % TJ];
+    const double w = w_tgt[p / TJ] * (w_occ ? w_occ[p % TJ] : 1.0);
     for (int r = 0; r < P2; ++r)
       for (int c = 0; c < 7; ++c) s[c] += w * partial[((long long)p * P2 + r) * 7 + c];
   }
@@ -193,6 +194,52 @@ __global__ void k_scale_rows(const double2* vx, const double* w, long long nrows
   }
 }
 
+// Real orbitals at Gamma: occupied slot p packs bands 2p and 2p+1 as
+//   cp[p] = s_2p c[2p] - i s_2p+1 c[2p+1]   (the second term absent past n_occ)
+// with s = sqrt(w) when fold (negative w sets the error flag and counts as 0),
+// else s = 1 and wp[p] = (w_2p, w_2p+1).
+__global__ void k_pack_real(const double2* c, const double* w, int n_occ, int npw_max, bool fold,
+                            double2* cp, double2* wp, int* err) {
+  const int n_slot = (n_occ + 1) / 2;
+  const long long total = (long long)n_slot * npw_max;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int slot = (int)(i / npw_max), g = (int)(i % npw_max);
+    const int b1 = 2 * slot, b2 = b1 + 1;
+    const bool has2 = b2 < n_occ;
+    const double w1 = w[b1], w2 = has2 ? w[b2] : 0.0;
+    double s1 = 1.0, s2 = has2 ? 1.0 : 0.0;
+    if (fold) {
+      if (w1 < 0.0 || w2 < 0.0) atomicOr(err, 2);
+      s1 = w1 > 0.0 ? sqrt(w1) : 0.0;
+      s2 = w2 > 0.0 ? sqrt(w2) : 0.0;
+    }
+    const double2 x = c[(long long)b1 * npw_max + g];
+    const double2 y = has2 ? c[(long long)b2 * npw_max + g] : make_double2(0.0, 0.0);
+    // s1 x - i s2 y
+    cp[i] = make_double2(s1 * x.x + s2 * y.y, s1 * x.y - s2 * y.x);
+    if (g == 0 && wp) wp[slot] = make_double2(w1, w2);
+  }
+}
+
+// Real part of V_x u: acc[a].y = 0 for every target a, and, when packed slot
+// accumulators are given, acc[b].x += slot[b/2].x (b even) or -slot[b/2].y (b odd)
+// for b < n_occ (the contributions that the k = q pair symmetry routes to band b).
+__global__ void k_real_combine(double2* acc, int n_tgt, const double2* slot, int n_occ, long long n3) {
+  const long long total = (long long)n_tgt * n3;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(i / n3);
+    const long long r = i % n3;
+    double x = acc[i].x;
+    if (slot && b < n_occ) {
+      const double2 v = slot[(long long)(b / 2) * n3 + r];
+      x += (b % 2 == 0) ? v.x : -v.y;
+    }
+    acc[i] = make_double2(x, 0.0);
+  }
+}
+
 }  // namespace xx
 
 using namespace xx;
@@ -228,6 +275,8 @@ struct xx_plan_s {
   size_t cap = 0;
   int ta_user = 0, tj_user = 0;
   bool pair_symmetry = true;
+  bool real_gamma = false;     // XX_OPT_REAL_GAMMA
+  bool gamma_closed = false;   // one k-point at Gamma whose basis holds -G for every G
   int ta_last = 0, tj_last = 0;
   const KernelTable* kt = nullptr;
   int* d_miller = nullptr;   // [nk][npw_max][3]
@@ -236,7 +285,7 @@ struct xx_plan_s {
   void* d_tw64 = nullptr;
   int* d_err = nullptr;
   DevBuf u_tgt, u_occ, inter, acc, vt, dvt, box, stage, dots, partial, dmu_acc, vx_tmp, u_bar,
-      stab;
+      stab, cpack, wpair, acc2;
   size_t ws_bytes = 0, peak_bytes = 0;
   long long launches = 0;
   // optional per-kernel-class timing with events on the launch stream
@@ -509,8 +558,13 @@ const char* grid_ptr(xx_plan p, bool shared, int q, int j, int n_occ, int n_tgt)
   return (const char*)p->u_occ.p + ((size_t)q * n_occ + j) * n3(p) * eb;
 }
 
+int run_apply_real(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, int n_occ,
+                   const void* c_tgt, int n_tgt, void* vx_out, cudaStream_t s);
+
+// real: take the real-orbital Gamma path (plan option XX_OPT_REAL_GAMMA)
 int run_apply(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, const double* w_occ,
-              int n_occ, const void* c_tgt, int n_tgt, void* vx_out, cudaStream_t s) {
+              int n_occ, const void* c_tgt, int n_tgt, void* vx_out, bool real, cudaStream_t s) {
+  if (real) return run_apply_real(p, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, vx_out, s);
   const bool shared = (c_occ == c_tgt && ld_occ == n_tgt && k0 == 0 && kn == p->nk);
   int st = build_grids(p, k0, kn, c_occ, ld_occ, n_occ, c_tgt, n_tgt, shared, s);
   if (st) return st;
@@ -598,6 +652,172 @@ int run_apply(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, const do
   return XX_OK;
 }
 
+// ---------------------------------------------- real orbitals at Gamma --
+// Every codensity conj(u_j) u_a is real and v(G) = v(-G) is real, so every W_aj
+// is real: occupied bands 2p and 2p+1 share one transform as the slot
+// u_2p - i u_2p+1 (codensity rho_a,2p + i rho_a,2p+1, potential W_a,2p + i W_a,2p+1).
+
+// Packed occupied grids of the n_occ occupied bands (k = 0) into p->u_occ, slot
+// weights into p->wpair; fold puts sqrt(w) into the slots instead.
+int build_packed(xx_plan p, const void* c_occ, const double* w_occ, int n_occ, bool fold,
+                 cudaStream_t s) {
+  const int n_slot = (n_occ + 1) / 2;
+  int st = ensure(p, p->cpack, (size_t)n_slot * p->npw_max * 16);
+  if (st) return st;
+  if ((st = ensure(p, p->wpair, (size_t)n_slot * 16))) return st;
+  if ((st = ensure(p, p->u_occ, (size_t)n_slot * n3(p) * elem_bytes(p)))) return st;
+  const long long total = (long long)n_slot * p->npw_max;
+  const long long want = (total + 255) / 256;
+  k_pack_real<<<(int)(want < 4096 ? want : 4096), 256, 0, s>>>(
+      (const double2*)c_occ, w_occ, n_occ, p->npw_max, fold, (double2*)p->cpack.p,
+      (double2*)p->wpair.p, p->d_err);
+  if ((st = launched(p, 1))) return st;
+  return sphere_to_grid(p, 0, (const double2*)p->cpack.p, n_slot, p->u_occ.p, s);
+}
+
+// Band tile of the pair-symmetric real path: even, at most TA targets and TJ slots.
+int real_tile(int TA, int TJ) {
+  int t = TA < 2 * TJ ? TA : 2 * TJ;
+  t &= ~1;
+  return t < 2 ? 2 : t;
+}
+
+// Visits the (target range, slot range) batches of the real path:
+// f(a0, ta, s0, ns, mirrored).  With sym, the occupied bands (the leading
+// targets) are cut into band tiles of T and only tile pairs J >= I are visited,
+// mirrored = J > I (the pair (J, I) is implied by symmetry); targets past
+// n_occ then meet every slot.  Without sym, every target batch meets every slot
+// batch.
+template <typename F>
+int for_real_tiles(int n_tgt, int n_occ, int TA, int TJ, bool sym, int T, F&& f) {
+  const int n_slot = (n_occ + 1) / 2;
+  int st;
+  int a_first = 0;
+  if (sym) {
+    for (int i0 = 0; i0 < n_occ; i0 += T) {
+      const int ti = (n_occ - i0) < T ? (n_occ - i0) : T;
+      for (int j0 = i0; j0 < n_occ; j0 += T) {
+        const int tj = (n_occ - j0) < T ? (n_occ - j0) : T;
+        if ((st = f(i0, ti, j0 / 2, (tj + 1) / 2, j0 > i0))) return st;
+      }
+    }
+    a_first = n_occ;
+  }
+  for (int a0 = a_first; a0 < n_tgt; a0 += TA) {
+    const int ta = (n_tgt - a0) < TA ? (n_tgt - a0) : TA;
+    for (int s0 = 0; s0 < n_slot; s0 += TJ) {
+      const int ns = (n_slot - s0) < TJ ? (n_slot - s0) : TJ;
+      if ((st = f(a0, ta, s0, ns, false))) return st;
+    }
+  }
+  return XX_OK;
+}
+
+int run_apply_real(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, int n_occ,
+                   const void* c_tgt, int n_tgt, void* vx_out, cudaStream_t s) {
+  const bool shared = (c_occ == c_tgt && ld_occ == n_tgt);
+  const size_t eb = elem_bytes(p);
+  const long long nn = n3(p);
+  int st = ensure(p, p->u_tgt, (size_t)n_tgt * nn * eb);
+  if (st) return st;
+  if ((st = sphere_to_grid(p, 0, (const double2*)c_tgt, n_tgt, p->u_tgt.p, s))) return st;
+  if ((st = build_packed(p, c_occ, w_occ, n_occ, false, s))) return st;
+  const int n_slot = (n_occ + 1) / 2;
+  int TA, TJ;
+  batch_shape(p, n_tgt, n_slot, &TA, &TJ);
+  p->ta_last = TA;
+  p->tj_last = TJ;
+  const bool sym = shared && p->pair_symmetry && n_occ > 1;
+  const int T = real_tile(TA, TJ);
+  long long npair = (long long)TA * TJ;
+  if (sym && (long long)T * (T / 2) > npair) npair = (long long)T * (T / 2);
+  if ((st = ensure(p, p->inter, (size_t)npair * p->N * P(p, 1) * P(p, 0) * eb))) return st;
+  if ((st = ensure(p, p->acc, (size_t)n_tgt * nn * 16))) return st;
+  cudaMemsetAsync(p->acc.p, 0, (size_t)n_tgt * nn * 16, s);
+  if (sym) {
+    if ((st = ensure(p, p->acc2, (size_t)n_slot * nn * 16))) return st;
+    cudaMemsetAsync(p->acc2.p, 0, (size_t)n_slot * nn * 16, s);
+  }
+  if ((st = kernel_table_for(p, 0, 0, false, s))) return st;
+  const KernelSet& ks = kset(p);
+  st = for_real_tiles(n_tgt, n_occ, TA, TJ, sym, T, [&](int a0, int ta, int s0, int ns, bool mirrored) {
+    PairArgs a = pair_args(p, ta, ns);
+    a.u_tgt = (const char*)p->u_tgt.p + (size_t)a0 * nn * eb;
+    a.u_occ = (const char*)p->u_occ.p + (size_t)s0 * nn * eb;
+    a.acc = (double2*)p->acc.p + (long long)a0 * nn;
+    a.w_pair = (const double2*)p->wpair.p + s0;
+    int e = prof_begin(p, s);
+    ks.pass_a(a, s);
+    prof_end(p, XX_PROF_PASS_A, e, s);
+    e = prof_begin(p, s);
+    ks.pass_b(a, s);
+    prof_end(p, XX_PROF_PASS_B, e, s);
+    e = prof_begin(p, s);
+    ks.pass_c_packed(a, s);
+    prof_end(p, XX_PROF_PASS_C, e, s);
+    if (!mirrored) return launched(p, 3);
+    // the slots of tile J receive -(w_a/N_k) u_a conj(W_a,slot) from the targets of
+    // tile I: real part for band 2p, minus the imaginary part for band 2p+1
+    PairArgs c = a;
+    c.w_tgt = w_occ + a0;
+    c.w_occ = nullptr;
+    c.acc = (double2*)p->acc2.p + (long long)s0 * nn;
+    e = prof_begin(p, s);
+    ks.pass_ct(c, s);
+    prof_end(p, XX_PROF_PASS_C, e, s);
+    return launched(p, 4);
+  });
+  if (st) return st;
+  const long long want = ((long long)n_tgt * nn + 255) / 256;
+  k_real_combine<<<(int)(want < 4096 ? want : 4096), 256, 0, s>>>(
+      (double2*)p->acc.p, n_tgt, sym ? (const double2*)p->acc2.p : nullptr, n_occ, nn);
+  if ((st = launched(p, 1))) return st;
+  return grid_to_sphere(p, 0, (const double2*)p->acc.p, n_tgt, (double2*)vx_out, s);
+}
+
+// Band-pair sums of the real path for dE/dmu (nsum = 1) and the strain
+// derivative (nsum = 7): sqrt(w) is folded into the slots, so a (target, slot)
+// pair carries w_2p S_a,2p + w_2p+1 S_a,2p+1 (the cross term sums to zero over
+// +-G for real codensities and an even table); reduced with w_a.
+int run_pair_sums_real(xx_plan p, const void* c, const double* w, int n_b, bool strain,
+                       cudaStream_t s) {
+  const size_t eb = elem_bytes(p);
+  const long long nn = n3(p);
+  int st = ensure(p, p->u_tgt, (size_t)n_b * nn * eb);
+  if (st) return st;
+  if ((st = sphere_to_grid(p, 0, (const double2*)c, n_b, p->u_tgt.p, s))) return st;
+  if ((st = build_packed(p, c, w, n_b, true, s))) return st;
+  const int n_slot = (n_b + 1) / 2;
+  int TA, TJ;
+  batch_shape(p, n_b, n_slot, &TA, &TJ);
+  const bool sym = p->pair_symmetry && n_b > 1;
+  const int T = real_tile(TA, TJ);
+  long long npair = (long long)TA * TJ;
+  if (sym && (long long)T * (T / 2) > npair) npair = (long long)T * (T / 2);
+  const int nsum = strain ? 7 : 1;
+  if ((st = ensure(p, p->inter, (size_t)npair * p->N * P(p, 1) * P(p, 0) * eb))) return st;
+  if ((st = ensure(p, p->partial, (size_t)npair * P(p, 1) * nsum * 8))) return st;
+  const KernelSet& ks = kset(p);
+  return for_real_tiles(n_b, n_b, TA, TJ, sym, T, [&](int a0, int ta, int s0, int ns, bool mirrored) {
+    PairArgs a = pair_args(p, ta, ns);
+    a.u_tgt = (const char*)p->u_tgt.p + (size_t)a0 * nn * eb;
+    a.u_occ = (const char*)p->u_occ.p + (size_t)s0 * nn * eb;
+    const double scale = mirrored ? 2.0 : 1.0;
+    ks.pass_a(a, s);
+    if (strain) {
+      a.dvt = p->stab.p;
+      ks.pass_b_strain(a, s);
+      k_strain_batch<<<1, kRedThreads, 0, s>>>((const double*)p->partial.p, P(p, 1), ta, ns, w + a0,
+                                               nullptr, scale, (double*)p->dmu_acc.p);
+    } else {
+      ks.pass_b_dmu(a, s);
+      k_dmu_batch<<<1, kRedThreads, 0, s>>>((const double*)p->partial.p, P(p, 1), ta, ns, w + a0,
+                                            nullptr, scale, (double*)p->dmu_acc.p);
+    }
+    return launched(p, 3);
+  });
+}
+
 int run_energy_reduce(xx_plan p, int k0, int kn, const void* c_tgt, const double* w_tgt, int n_tgt,
                       const void* vx, double* ex_out, cudaStream_t s) {
   const int rows = kn * n_tgt;
@@ -614,7 +834,17 @@ int run_energy_reduce(xx_plan p, int k0, int kn, const void* c_tgt, const double
 // dE/dmu accumulation: codensities recomputed (pass A) + forward z with dv/dmu (pass B')
 int run_dmu(xx_plan p, const void* c, const double* w, int n_b, double grad, double* dmu_out,
             cudaStream_t s) {
-  int st = build_grids(p, 0, p->nk, c, n_b, n_b, c, n_b, true, s);
+  const double factor = -0.5 * kSpin * p->omega / ((double)p->nk * (double)p->nk) * grad;
+  int st;
+  if (p->real_gamma) {
+    if ((st = ensure(p, p->dmu_acc, 8))) return st;
+    cudaMemsetAsync(p->dmu_acc.p, 0, 8, s);
+    if ((st = kernel_table_for(p, 0, 0, true, s))) return st;
+    if ((st = run_pair_sums_real(p, c, w, n_b, false, s))) return st;
+    k_scale_scalar<<<1, 32, 0, s>>>((const double*)p->dmu_acc.p, factor, dmu_out);
+    return launched(p, 1);
+  }
+  st = build_grids(p, 0, p->nk, c, n_b, n_b, c, n_b, true, s);
   if (st) return st;
   int TA, TJ;
   batch_shape(p, n_b, n_b, &TA, &TJ);
@@ -654,50 +884,62 @@ int run_dmu(xx_plan p, const void* c, const double* w, int n_b, double grad, dou
         }
       }
     }
-  const double factor = -0.5 * kSpin * p->omega / ((double)p->nk * (double)p->nk) * grad;
   k_scale_scalar<<<1, 32, 0, s>>>((const double*)p->dmu_acc.p, factor, dmu_out);
   return launched(p, 1);
 }
 
 // Strain derivative of E_x[c] at fixed coefficients: pass A + forward z with the
 // seven tables of k_strain_tab, reduced with w_a w_j (pair symmetry on k = q).
+// the seven strain tables of k - q into p->stab
+int strain_tables(xx_plan p, int k, int q, cudaStream_t s) {
+  const long long nbox = (long long)P(p, 0) * P(p, 1) * P(p, 2);
+  int st = ensure(p, p->stab, (size_t)7 * nbox * (p->prec == XX_FP64 ? 8 : 4));
+  if (st) return st;
+  VtabArgs va{};
+  std::memcpy(va.Bm, p->B, sizeof(va.Bm));
+  std::memcpy(va.M, p->M, sizeof(va.M));
+  for (int i = 0; i < 3; ++i) va.d[i] = p->kfrac[3 * k + i] - p->kfrac[3 * q + i];
+  va.h1 = p->h[0];
+  va.h2 = p->h[1];
+  va.h3 = p->h[2];
+  va.P1 = P(p, 0);
+  va.P2 = P(p, 1);
+  va.P3 = P(p, 2);
+  va.kernel = p->kernel;
+  va.mu = p->mu;
+  va.inv_n = 1.0 / (double)n3(p);
+  va.inv_n2 = va.inv_n * va.inv_n;
+  const int blocks = (int)((nbox + 255) / 256);
+  if (p->prec == XX_FP64)
+    k_strain_tab<double><<<blocks, 256, 0, s>>>((double*)p->stab.p, va);
+  else
+    k_strain_tab<float><<<blocks, 256, 0, s>>>((float*)p->stab.p, va);
+  return launched(p, 1);
+}
+
 int run_strain(xx_plan p, const void* c, const double* w, int n_b, double* out9, double* ex_out,
                cudaStream_t s) {
-  int st = build_grids(p, 0, p->nk, c, n_b, n_b, c, n_b, true, s);
+  int st = ensure(p, p->dmu_acc, 7 * 8);
+  if (st) return st;
+  cudaMemsetAsync(p->dmu_acc.p, 0, 7 * 8, s);
+  if (p->real_gamma) {
+    if ((st = strain_tables(p, 0, 0, s))) return st;
+    if ((st = run_pair_sums_real(p, c, w, n_b, true, s))) return st;
+    k_strain_final<<<1, 32, 0, s>>>((const double*)p->dmu_acc.p, p->omega, p->nk, out9, ex_out);
+    return launched(p, 1);
+  }
+  st = build_grids(p, 0, p->nk, c, n_b, n_b, c, n_b, true, s);
   if (st) return st;
   int TA, TJ;
   batch_shape(p, n_b, n_b, &TA, &TJ);
   const size_t eb = elem_bytes(p);
-  const long long nbox = (long long)P(p, 0) * P(p, 1) * P(p, 2);
   if ((st = ensure(p, p->inter, (size_t)TA * TJ * p->N * P(p, 1) * P(p, 0) * eb))) return st;
   if ((st = ensure(p, p->partial, (size_t)TA * TJ * P(p, 1) * 7 * 8))) return st;
-  if ((st = ensure(p, p->stab, (size_t)7 * nbox * (p->prec == XX_FP64 ? 8 : 4)))) return st;
-  if ((st = ensure(p, p->dmu_acc, 7 * 8))) return st;
-  cudaMemsetAsync(p->dmu_acc.p, 0, 7 * 8, s);
   const KernelSet& ks = kset(p);
   const int T = TJ < TA ? TJ : TA;
   for (int k = 0; k < p->nk; ++k)
     for (int q = 0; q < p->nk; ++q) {
-      VtabArgs va{};
-      std::memcpy(va.Bm, p->B, sizeof(va.Bm));
-      std::memcpy(va.M, p->M, sizeof(va.M));
-      for (int i = 0; i < 3; ++i) va.d[i] = p->kfrac[3 * k + i] - p->kfrac[3 * q + i];
-      va.h1 = p->h[0];
-      va.h2 = p->h[1];
-      va.h3 = p->h[2];
-      va.P1 = P(p, 0);
-      va.P2 = P(p, 1);
-      va.P3 = P(p, 2);
-      va.kernel = p->kernel;
-      va.mu = p->mu;
-      va.inv_n = 1.0 / (double)n3(p);
-      va.inv_n2 = va.inv_n * va.inv_n;
-      const int blocks = (int)((nbox + 255) / 256);
-      if (p->prec == XX_FP64)
-        k_strain_tab<double><<<blocks, 256, 0, s>>>((double*)p->stab.p, va);
-      else
-        k_strain_tab<float><<<blocks, 256, 0, s>>>((float*)p->stab.p, va);
-      if ((st = launched(p, 1))) return st;
+      if ((st = strain_tables(p, k, q, s))) return st;
       const bool diag = p->pair_symmetry && q == k && n_b > 1;
       const int SA = diag ? T : TA, SJ = diag ? T : TJ;
       for (int a0 = 0; a0 < n_b; a0 += SA) {
@@ -797,7 +1039,7 @@ const char* xx_status_string(int status) {
     case XX_ERR_GRID_ALIASING: return "FFT grid too small: an axis has N < 4 n_max + 1 (codensity wrap-around)";
     case XX_ERR_OUT_OF_MEMORY: return "out of device memory";
     case XX_ERR_CUDA: return "CUDA error";
-    case XX_ERR_DEVICE_FLAG: return "device-side check failed (inconsistent basis data)";
+    case XX_ERR_DEVICE_FLAG: return "device-side check failed (inconsistent basis data or a negative occupation)";
     case XX_ERR_TIMEOUT: return "timed out waiting for the stream";
     case XX_ERR_NO_DEVICE: return "no usable CUDA device";
     case XX_ERR_SIZE_LIMIT: return "size exceeds the fixed scratch of the no-allocation entry point (XX_NOALLOC_MAX_ROWS)";
@@ -876,6 +1118,19 @@ int xx_create(xx_plan* out, const double* lattice, const int* grid, int nk, cons
     p->nmax[ax] = nmax[ax];
     p->h[ax] = 2 * nmax[ax];
   }
+  // real orbitals need a single k-point at Gamma whose basis is closed under G -> -G
+  if (nk == 1 && kfrac[0] == 0.0 && kfrac[1] == 0.0 && kfrac[2] == 0.0) {
+    std::vector<long long> keys(npw[0]);
+    auto key = [](long long a, long long b, long long c) { return ((a + 8192) * 16384 + (b + 8192)) * 16384 + (c + 8192); };
+    for (int g = 0; g < npw[0]; ++g)
+      keys[g] = key(miller[3 * g], miller[3 * g + 1], miller[3 * g + 2]);
+    std::sort(keys.begin(), keys.end());
+    bool closed = std::adjacent_find(keys.begin(), keys.end()) == keys.end();
+    for (int g = 0; g < npw[0] && closed; ++g)
+      closed = std::binary_search(keys.begin(), keys.end(),
+                                  key(-miller[3 * g], -miller[3 * g + 1], -miller[3 * g + 2]));
+    p->gamma_closed = closed;
+  }
   p->kernel = kernel_type;
   p->mu = mu;
   p->prec = precision;
@@ -916,7 +1171,7 @@ int xx_destroy(xx_plan p) {
   cudaDeviceSynchronize();
   DevBuf* bufs[] = {&p->u_tgt, &p->u_occ, &p->inter, &p->acc, &p->vt, &p->dvt, &p->box,
                     &p->stage, &p->dots, &p->partial, &p->dmu_acc, &p->vx_tmp, &p->u_bar,
-                    &p->stab};
+                    &p->stab, &p->cpack, &p->wpair, &p->acc2};
   for (DevBuf* b : bufs) release(*b);
   if (p->d_miller) cudaFree(p->d_miller);
   if (p->d_npw) cudaFree(p->d_npw);
@@ -931,9 +1186,13 @@ int xx_destroy(xx_plan p) {
   return XX_OK;
 }
 
-int xx_apply_range(xx_plan p, int k_first, int k_count, const void* c_occ, int ld_occ,
-                   const double* w_occ, int n_occ, const void* c_tgt, int n_tgt, void* vx_out,
-                   void* stream) {
+}  // extern "C"
+
+namespace {
+
+int apply_range(xx_plan p, int k_first, int k_count, const void* c_occ, int ld_occ,
+                const double* w_occ, int n_occ, const void* c_tgt, int n_tgt, void* vx_out,
+                bool real, void* stream) {
   if (!p || n_occ < 0 || n_tgt < 0 || k_first < 0 || k_count < 0 || k_first + k_count > p->nk)
     return XX_ERR_INVALID_ARGUMENT;
   if (ld_occ == 0) ld_occ = n_occ;
@@ -946,7 +1205,19 @@ int xx_apply_range(xx_plan p, int k_first, int k_count, const void* c_occ, int l
     return cuda_status(e);
   }
   if (bad_ptr(c_occ) || bad_ptr(w_occ)) return XX_ERR_INVALID_ARGUMENT;
-  return run_apply(p, k_first, k_count, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, vx_out, s);
+  return run_apply(p, k_first, k_count, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, vx_out, real, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int xx_apply_range(xx_plan p, int k_first, int k_count, const void* c_occ, int ld_occ,
+                   const double* w_occ, int n_occ, const void* c_tgt, int n_tgt, void* vx_out,
+                   void* stream) {
+  if (!p) return XX_ERR_INVALID_ARGUMENT;
+  return apply_range(p, k_first, k_count, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, vx_out,
+                     p->real_gamma, stream);
 }
 
 int xx_apply(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, int n_occ,
@@ -1007,7 +1278,8 @@ int xx_apply_backward(xx_plan p, const void* c, const double* w, int n_b, const 
     const void* v = vx;
     if (!v) {
       if ((st = ensure(p, p->vx_tmp, (size_t)p->nk * n_b * p->npw_max * 16))) return st;
-      if ((st = run_apply(p, 0, p->nk, c, n_b, w, n_b, c, n_b, p->vx_tmp.p, s))) return st;
+      if ((st = run_apply(p, 0, p->nk, c, n_b, w, n_b, c, n_b, p->vx_tmp.p, p->real_gamma, s)))
+        return st;
       v = p->vx_tmp.p;
     }
     const long long rows = (long long)p->nk * n_b;
@@ -1090,8 +1362,10 @@ int xx_apply_vjp(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, 
     if (o && (o == c_occ || o == c_tgt || o == ybar)) return XX_ERR_INVALID_ARGUMENT;
   int st;
   if (grad_tgt_out && n_tgt > 0) {
-    // V_x is Hermitian: dL/dc_tgt* = V_x ybar
-    if ((st = xx_apply(p, c_occ, ld_occ, w_occ, n_occ, ybar, n_tgt, grad_tgt_out, stream))) return st;
+    // V_x is Hermitian: dL/dc_tgt* = V_x ybar (a complex cotangent: general path)
+    if ((st = apply_range(p, 0, p->nk, c_occ, ld_occ, w_occ, n_occ, ybar, n_tgt, grad_tgt_out,
+                          false, stream)))
+      return st;
   }
   if (grad_occ_out && n_occ > 0) {
     if (n_tgt == 0)
@@ -1147,6 +1421,10 @@ int xx_set_option(xx_plan p, int option, long long value) {
   switch (option) {
     case XX_OPT_PAIR_SYMMETRY:
       p->pair_symmetry = value != 0;
+      return XX_OK;
+    case XX_OPT_REAL_GAMMA:
+      if (value != 0 && !p->gamma_closed) return XX_ERR_INVALID_ARGUMENT;
+      p->real_gamma = value != 0;
       return XX_OK;
     default:
       return XX_ERR_INVALID_ARGUMENT;

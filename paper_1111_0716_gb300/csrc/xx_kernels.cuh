@@ -33,6 +33,7 @@ struct PairArgs {
   double2* acc;          // [TA][N^3] FP64 accumulators of the target batch
   const double* w_occ;   // [TJ] occupations of the occupied batch
   const double* w_tgt;   // [TA] occupations of the target batch
+  const double2* w_pair; // [TJ] (w_2p, w_2p+1) of packed occupied slots (real orbitals)
   double* partial;       // [TA*TJ][P2] mu-gradient partial sums
   const void* tw;        // [N] exp(-2 pi i e / N) in the pass precision
   long long u_tgt_stride;  // elements between consecutive target grids
@@ -559,7 +560,11 @@ __global__ void __launch_bounds__(NT) k_pass_b_dmu(PairArgs p) {
 
 // Pass C: grid (TA, N); CTA (ta, z) accumulates -(w_j/N_q) u_j W over the
 // occupied batch in registers and adds the plane into the FP64 accumulator.
-template <int N, typename T>
+// PACKED (real orbitals at Gamma): occupied slot p holds u_2p - i u_2p+1, so W
+// holds W_a,2p + i W_a,2p+1 and only the real part is accumulated,
+//   acc_a.x += -(1/N_q) (w_2p u_2p W_a,2p + w_2p+1 u_2p+1 W_a,2p+1)
+//            = -(1/N_q) (w_2p Re(u) Re(W) - w_2p+1 Im(u) Im(W)).
+template <int N, typename T, bool PACKED>
 __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_c(PairArgs p) {
   using C = cplx<T>;
   using G = PlaneCfg<N, T>;
@@ -586,15 +591,28 @@ __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_c(PairArgs p) {
     const C* in = reinterpret_cast<const C*>(p.inter) +
                   ((long long)(ta * p.TJ + tj) * N + z) * (long long)p.P2 * p.P1;
     const C* uj = reinterpret_cast<const C*>(p.u_occ) + tj * p.u_occ_stride + z * plane;
-    const T cf = (T)(p.coef * p.w_occ[tj]);
+    T cf, cf2;
+    if (PACKED) {
+      const double2 w = p.w_pair[tj];
+      cf = (T)(p.coef * w.x);
+      cf2 = (T)(-p.coef * w.y);
+    } else {
+      cf = (T)(p.coef * p.w_occ[tj]);
+      cf2 = (T)0;
+    }
     const long long pbytes = (long long)p.P2 * p.P1 * (long long)sizeof(C);
     const C* next = tj + 1 < p.TJ ? in + (long long)N * p.P2 * p.P1 : nullptr;
     plane_inverse<N, T, false>(
         tw, tw2, s0, s1, p.h1, p.P1, p.h2, [&](int kyb, int kxb) { return in[kyb * P1 + kxb]; },
         [&](int i, int k2, int y, int x, C v) {
-          const C t = cmul(uj[y * N + x], v);
-          acc[i][k2].x += cf * t.x;
-          acc[i][k2].y += cf * t.y;
+          const C u = uj[y * N + x];
+          if (PACKED) {
+            acc[i][k2].x += cf * (u.x * v.x) + cf2 * (u.y * v.y);
+          } else {
+            const C t = cmul(u, v);
+            acc[i][k2].x += cf * t.x;
+            acc[i][k2].y += cf * t.y;
+          }
         },
         uj, plane * (long long)sizeof(C), next, pbytes);
   }
@@ -610,10 +628,14 @@ __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_c(PairArgs p) {
 #pragma unroll
       for (int k2 = 0; k2 < B; ++k2) {
         double2* o = dst + y * N + k1 + A * k2;
-        double2 cur = *o;
-        cur.x += (double)acc[i][k2].x;
-        cur.y += (double)acc[i][k2].y;
-        *o = cur;
+        if (PACKED) {
+          o->x += (double)acc[i][k2].x;
+        } else {
+          double2 cur = *o;
+          cur.x += (double)acc[i][k2].x;
+          cur.y += (double)acc[i][k2].y;
+          *o = cur;
+        }
       }
     }
   }

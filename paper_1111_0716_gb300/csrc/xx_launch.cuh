@@ -15,6 +15,7 @@ struct KernelSet {
   void (*pass_b_dmu)(const PairArgs&, cudaStream_t);
   void (*pass_b_strain)(const PairArgs&, cudaStream_t);
   void (*pass_c)(const PairArgs&, cudaStream_t);
+  void (*pass_c_packed)(const PairArgs&, cudaStream_t);
   void (*pass_ct)(const PairArgs&, cudaStream_t);
   void (*s2g_z)(const GridArgs&, cudaStream_t);
   void (*s2g_xy)(const GridArgs&, cudaStream_t);
@@ -55,11 +56,11 @@ template <int N, typename T> void launch_pass_b_strain(const PairArgs& p, cudaSt
   allow_smem(k_pass_b_strain<N, kThreads, T>, sm);
   k_pass_b_strain<N, kThreads, T><<<dim3(p.P2, p.TA * p.TJ), kThreads, sm, s>>>(p);
 }
-template <int N, typename T> void launch_pass_c(const PairArgs& p, cudaStream_t s) {
+template <int N, typename T, bool PACKED> void launch_pass_c(const PairArgs& p, cudaStream_t s) {
   using G = PlaneCfg<N, T>;
   const size_t sm = G::smem();
-  allow_smem(k_pass_c<N, T>, sm);
-  k_pass_c<N, T><<<dim3(p.TA, N), G::NT, sm, s>>>(p);
+  allow_smem(k_pass_c<N, T, PACKED>, sm);
+  k_pass_c<N, T, PACKED><<<dim3(p.TA, N), G::NT, sm, s>>>(p);
 }
 template <int N, typename T> void launch_pass_ct(const PairArgs& p, cudaStream_t s) {
   using G = PlaneCfg<N, T>;
@@ -94,10 +95,12 @@ template <int N> const KernelTable* make_table() {
   static const KernelTable t = {
       N,
       {launch_pass_a<N, float>, launch_pass_b<N, float>, launch_pass_b_dmu<N, float>,
-       launch_pass_b_strain<N, float>, launch_pass_c<N, float>, launch_pass_ct<N, float>, launch_s2g_z<N, float>,
+       launch_pass_b_strain<N, float>, launch_pass_c<N, float, false>, launch_pass_c<N, float, true>,
+       launch_pass_ct<N, float>, launch_s2g_z<N, float>,
        launch_s2g_xy<N, float>},
       {launch_pass_a<N, double>, launch_pass_b<N, double>, launch_pass_b_dmu<N, double>,
-       launch_pass_b_strain<N, double>, launch_pass_c<N, double>, launch_pass_ct<N, double>, launch_s2g_z<N, double>,
+       launch_pass_b_strain<N, double>, launch_pass_c<N, double, false>, launch_pass_c<N, double, true>,
+       launch_pass_ct<N, double>, launch_s2g_z<N, double>,
        launch_s2g_xy<N, double>},
       launch_g2s_xy<N>,
       launch_g2s_z<N>};

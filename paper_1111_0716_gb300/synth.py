@@ -184,12 +184,64 @@ def random_orbitals(rng: np.random.Generator, lattice, kfrac, npw, miller, nb,
     return out
 
 
+def minus_g_index(miller: np.ndarray) -> np.ndarray:
+    """Row of -m for every Miller row m of one basis set (ValueError if one is missing)."""
+    pos = {tuple(int(v) for v in m): i for i, m in enumerate(miller)}
+    try:
+        return np.array([pos[tuple(-int(v) for v in m)] for m in miller], dtype=np.int64)
+    except KeyError:
+        raise ValueError("basis set is not closed under G -> -G") from None
+
+
+def random_real_orbitals(rng: np.random.Generator, lattice, npw, miller, nb,
+                         envelope: float = 8.0) -> np.ndarray:
+    """Gamma-point orbitals that are real in real space, orthonormal: c(-G) = conj c(G).
+
+    Each orbital is drawn as real coefficients x on the real basis {1 at G = 0;
+    sqrt2 cos(G.r), sqrt2 sin(G.r) for each pair (G, -G) with G's first nonzero
+    Miller component positive}, iid N(0, 1) times the envelope, orthonormalised
+    (QR in real arithmetic, diagonal of R positive), then mapped to plane waves by
+    c(G) = (x_cos - i x_sin)/sqrt2, c(-G) = (x_cos + i x_sin)/sqrt2, c(0) = x_0.
+    The map is unitary, so orthonormal x give orthonormal c.  Draw order: band,
+    then real basis function in lexicographic order of G (cos before sin).
+    """
+    B = reciprocal(lattice)
+    n = int(npw[0])
+    if nb > n:
+        raise ValueError("more bands than plane waves")
+    m = miller[0, :n]
+    neg = minus_g_index(m)
+    first = np.array([next((int(v) for v in row if v != 0), 0) for row in m])
+    zero = np.flatnonzero(first == 0)
+    pos = np.flatnonzero(first > 0)
+    g = m @ B
+    env = np.exp(-np.einsum("ij,ij->i", g, g) / envelope)
+    # real basis functions in lexicographic order of their G: G = 0 (if present), then pairs
+    scale = np.concatenate([env[zero], np.repeat(env[pos], 2)])
+    x = rng.standard_normal((nb, scale.size)) * scale[None, :]
+    q, r = np.linalg.qr(x.T)
+    q = q * np.sign(np.diag(r))[None, :]
+    x = q.T                                            # (nb, n) orthonormal rows
+    out = np.zeros((1, nb, miller.shape[1]), dtype=np.complex128)
+    nz = zero.size
+    out[0][:, zero] = x[:, :nz]
+    xc, xs = x[:, nz::2], x[:, nz + 1::2]
+    out[0][:, pos] = (xc - 1j * xs) / math.sqrt(2.0)
+    out[0][:, neg[pos]] = (xc + 1j * xs) / math.sqrt(2.0)
+    return out
+
+
 def make_workload(name, lattice, grid, kfrac, gcut, n_occ, n_tgt, w_occ_values,
-                  seed, kernel=KERNEL_HSE, mu=HSE06_MU) -> Workload:
+                  seed, kernel=KERNEL_HSE, mu=HSE06_MU, real=False) -> Workload:
     rng = np.random.Generator(np.random.PCG64(seed))
     npw, miller = _basis(lattice, kfrac, gcut)
     nb = max(n_occ, n_tgt)
-    coeff = random_orbitals(rng, lattice, kfrac, npw, miller, nb)
+    if real:
+        if kfrac.shape[0] != 1 or np.any(kfrac != 0.0):
+            raise ValueError("real orbitals need a Gamma-only mesh")
+        coeff = random_real_orbitals(rng, lattice, npw, miller, nb)
+    else:
+        coeff = random_orbitals(rng, lattice, kfrac, npw, miller, nb)
     w = np.zeros((kfrac.shape[0], nb), dtype=np.float64)
     w[:, :n_occ] = np.asarray(w_occ_values, dtype=np.float64)[None, :]
     return Workload(name=name, lattice=lattice, grid=tuple(int(g) for g in grid),
@@ -261,6 +313,29 @@ def plane_wave_cell(shell: int, grid: int = 32, L: float = 10.0) -> Workload:
                     npw=np.array([n], dtype=np.int32), miller=m[None].copy(),
                     coeff=coeff, w=np.ones((1, n)), n_occ=n, n_tgt=n,
                     kernel=KERNEL_COULOMB, mu=0.0, seed=None)
+
+
+def real_tiny_cubic(seed: int = 61, grid: int = 24, n_occ: int = 7, n_tgt: int = 9,
+                    kernel=KERNEL_HSE) -> Workload:
+    """tiny_cubic with real (Gamma-point) orbitals, an odd occupied count and extra targets."""
+    L = 10.0
+    w = [1.0] * (n_occ - 1) + [0.5]
+    return make_workload("real-cubic-L10-%d^3-%do-%dt" % (grid, n_occ, n_tgt), cubic_lattice(L),
+                         (grid,) * 3, np.zeros((1, 3)), 5.0 * 2.0 * math.pi / L, n_occ, n_tgt,
+                         w, seed, kernel=kernel, real=True)
+
+
+def real_alpha_cell(seed: int = 62) -> Workload:
+    """alpha-boron-sized rhombohedral cell at Gamma only, 48^3, real orbitals, 18 occ / 24 tgt."""
+    return make_workload("real-alpha-B12-48^3-G", rhombohedral_lattice(9.56, 58.06), (48,) * 3,
+                         np.zeros((1, 3)), 4.5, 18, 24, [1.0] * 16 + [0.5] * 2, seed, real=True)
+
+
+def real_beta_cell(seed: int = 63) -> Workload:
+    """beta-boron-sized rhombohedral cell at Gamma only, 96^3, real orbitals, 160 occ / 192 tgt."""
+    w = [1.0] * 150 + [0.5] * 10
+    return make_workload("real-beta-B106-96^3-G", rhombohedral_lattice(19.17, 65.2), (96,) * 3,
+                         np.zeros((1, 3)), 4.5, 160, 192, w, seed, real=True)
 
 
 def all_parity_workloads() -> List[Workload]:

@@ -39,6 +39,7 @@ EXPORTS = ("xx_create", "xx_destroy", "xx_apply", "xx_apply_range", "xx_energy",
            "xx_profile_read", "xx_plan_info", "xx_status_string", "xx_energy_from_vx_noalloc",
            "xx_run_many", "xx_apply_vjp", "xx_set_option", "xx_strain_derivative")
 XX_OPT_PAIR_SYMMETRY = 0
+XX_OPT_REAL_GAMMA = 1
 
 PROF_CLASSES = ("pass_a", "pass_b", "pass_c", "sphere_to_grid", "grid_to_sphere",
                 "kernel_table", "reduce", "pass_b_dmu")
@@ -319,6 +320,10 @@ class Plan:
 
     def set_pair_symmetry(self, enable: bool):
         xx_set_option(self.handle, XX_OPT_PAIR_SYMMETRY, 1 if enable else 0)
+
+    def set_real_gamma(self, enable: bool):
+        """Declare the orbitals of later calls real in real space (Gamma-only plans)."""
+        xx_set_option(self.handle, XX_OPT_REAL_GAMMA, 1 if enable else 0)
 
     def set_batch(self, targets: int, occupied: int):
         xx_set_batch(self.handle, targets, occupied)

@@ -280,3 +280,44 @@ def test_dc_gradient_matches_finite_difference(oracle_mod):
         fd = (ep - em) / (2 * h)
         an = 2.0 * np.real(np.vdot(dlt, grad))
         assert abs(fd - an) <= 1e-7 * max(abs(an), 1e-3 * np.abs(grad).max())
+
+
+# ---------------------------------------------------- real orbitals at Gamma
+
+def test_synthetic_real_orbitals_are_real_and_orthonormal():
+    """The real-orbital generator: c(-G) = conj c(G), u(r) real, <c_a|c_b> = delta_ab."""
+    wl = synth.real_tiny_cubic()
+    n = int(wl.npw[0])
+    c = wl.coeff[0, :, :n]
+    assert np.abs(c.conj() @ c.T - np.eye(c.shape[0])).max() <= 1e-13
+    neg = synth.minus_g_index(wl.miller[0, :n])
+    assert np.array_equal(c[:, neg], c.conj())
+    N = wl.grid[0]
+    box = np.zeros((c.shape[0], N, N, N), dtype=np.complex128)
+    m = wl.miller[0, :n] % N
+    box[:, m[:, 0], m[:, 1], m[:, 2]] = c
+    u = np.fft.ifftn(box, axes=(1, 2, 3))
+    assert np.abs(u.imag).max() <= 1e-14 * np.abs(u.real).max()
+
+
+@pytest.mark.parametrize("kernel", [synth.KERNEL_HSE, synth.KERNEL_COULOMB])
+def test_exchange_of_real_orbitals_is_real(oracle_mod, kernel):
+    """With real occupied orbitals and a real kernel even in G, V_x maps real
+    functions to real functions: (V_x c)(-G) = conj (V_x c)(G) for real targets."""
+    wl = synth.real_tiny_cubic(n_occ=3, n_tgt=4, kernel=kernel)
+    vx = oracle_mod.apply(wl)[0]
+    n = int(wl.npw[0])
+    neg = synth.minus_g_index(wl.miller[0, :n])
+    assert np.abs(vx[:, neg] - vx[:, :n].conj()).max() <= 1e-13 * np.abs(vx).max()
+    # and every pair potential is real, W_aj = W_ja (the two bands of a packed
+    # transform are its real and imaginary parts)
+    m = wl.miller[0, :n]
+    u = [oracle_mod.sphere_to_grid(wl.lattice, wl.grid, m, wl.coeff[0, b, :n]) for b in range(3)]
+    d = np.zeros(3)
+    W01 = oracle_mod.pair_potential(wl.lattice, wl.grid, d, kernel, wl.mu, u[1], u[0])
+    W10 = oracle_mod.pair_potential(wl.lattice, wl.grid, d, kernel, wl.mu, u[0], u[1])
+    assert np.abs(W01.imag).max() <= 1e-13 * np.abs(W01.real).max()
+    assert np.abs(W01 - W10).max() <= 1e-13 * np.abs(W01).max()
+    Wp = oracle_mod.pair_potential(wl.lattice, wl.grid, d, kernel, wl.mu, u[1] - 1j * u[2], u[0])
+    W02 = oracle_mod.pair_potential(wl.lattice, wl.grid, d, kernel, wl.mu, u[2], u[0])
+    assert np.abs(Wp - (W01 + 1j * W02)).max() <= 1e-13 * np.abs(Wp).max()
