@@ -15,6 +15,8 @@ Printed as one JSON line (rank 0):
              against the measured HBM copy bandwidth
   cpu_baseline  the FP64 CPU oracle, as it stands, on a bounded sample
   fp64_slice    the all-FP64 GPU path on a slice of the same workload
+  real_gamma    the real-orbital Gamma path against the general path on the same
+                cell at the Gamma point only (real orbitals, 30,720 pairs)
   --impl reference  times the oracle as the reference arm.
 Multi-GPU (torchrun): each rank runs an independent workload (its own seed),
 weak scaling; value = all ranks' pairs / max-over-ranks time.
@@ -205,6 +207,39 @@ def profile_case(args):
                       "workspace_gb": info["peak_workspace_bytes"] / 1e9}))
 
 
+def real_gamma_leg(xx, torch, stream, reps=3):
+    """E_x step on the Gamma-only cell with real orbitals: general path (k = q pair
+    symmetry) against the real-orbital path (two occupied bands per transform)."""
+    from paper_1111_0716_gb300 import synth
+    wl = synth.real_beta_cell()
+    c = torch.from_numpy(wl.c_tgt.copy()).cuda()
+    wo = torch.from_numpy(wl.w_occ.copy()).cuda()
+    wt = torch.from_numpy(wl.w_tgt.copy()).cuda()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    out = {}
+    for real in (False, True):
+        plan = xx.Plan.from_workload(wl, precision=xx.XX_FP32_MIXED)
+        plan.set_real_gamma(real)
+        ex, vx = plan.energy(c, wo, c, wt, shared=True, stream=stream)
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            g0.record(stream)
+            plan.energy(c, wo, c, wt, vx_out=vx, ex_out=ex, shared=True, stream=stream)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(g0.elapsed_time(g1) / 1e3)
+        plan.sync(timeout_s=60.0, stream=stream)
+        out[real] = (float(np.median(ts)), float(ex[0].item()))
+        plan.close()
+    pairs = wl.pair_count()
+    return {"value": pairs / out[True][0], "unit": UNIT, "general_path": pairs / out[False][0],
+            "E_x_rel_diff": abs(out[True][1] - out[False][1]) / abs(out[False][1]),
+            "sample": "%s: 1 k-point, %d occupied x %d targets = %d pairs, FP32-mixed, median of %d"
+                      % (wl.name, wl.n_occ, wl.n_tgt, pairs, reps)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,6 +251,7 @@ def main():
                          "about 10 s on 16 cores)")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 slice")
+    ap.add_argument("--no-real", action="store_true", help="skip the real-orbital Gamma leg")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one small slice of the workload (k=0, 16 targets, 32 occupied "
                          "bands, all q) once and exit: the case ncu captures")
@@ -409,6 +445,9 @@ def main():
                               % (nt, no, p_slice)}
         p64.close()
         p32.close()
+
+    if rank == 0 and not args.no_real:
+        line["real_gamma"] = real_gamma_leg(xx, torch, stream)
 
     if rank == 0 and args.with_vjp:
         nt = 16
