@@ -103,9 +103,13 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_beta_boron_96.json")
 
 
 def kernel_source_hash():
-    """Hash of the CUDA sources: recorded DRAM traffic is only valid for these kernels."""
+    """Hash of the device-code sources (the kernels, their FFT building blocks and
+    launchers; not the host loops of xx_api.cu): recorded DRAM traffic per launch
+    is only valid for these kernels."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1111_0716_gb300", "csrc", "*.cu*"))):
+    csrc = os.path.join(ROOT, "paper_1111_0716_gb300", "csrc")
+    files = glob.glob(os.path.join(csrc, "*.cuh")) + glob.glob(os.path.join(csrc, "xx_n*.cu"))
+    for f in sorted(files):
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -123,24 +127,51 @@ def recorded_traffic(kernel, batch):
     return d.get("bytes_per_launch", {}).get(kernel)
 
 
-def pass_bytes_per_step(wl, TA, TJ, elem=8):
+def batch_schedule(nk, n_occ, n_tgt, TA, TJ, sym=True, cross=True):
+    """The band-pair launches of one xx_energy call with shared grids, in the
+    host loop's order: (kind, targets, occupied) with kind "full" (passes A, B,
+    C) or "mirrored" (passes A, B, C and the role-swapped pass C)."""
+    out = []
+    T = min(TA, TJ)
+    for k in range(nk):
+        for q in range(nk):
+            diag = sym and q == k
+            upper = sym and cross and q > k
+            lower = sym and cross and q < k
+            if diag:
+                for i0 in range(0, n_occ, T):
+                    for j0 in range(i0, n_occ, T):
+                        out.append(("mirrored" if j0 > i0 else "full",
+                                    min(T, n_occ - i0), min(T, n_occ - j0)))
+            if upper:
+                for a0 in range(0, n_occ, TA):
+                    for j0 in range(0, n_occ, TJ):
+                        out.append(("mirrored", min(TA, n_occ - a0), min(TJ, n_occ - j0)))
+            for a0 in range(n_occ if (diag or upper or lower) else 0, n_tgt, TA):
+                for j0 in range(0, n_occ, TJ):
+                    out.append(("full", min(TA, n_tgt - a0), min(TJ, n_occ - j0)))
+    return out
+
+
+def pass_bytes_per_step(wl, schedule, elem=8):
     """Algorithmic HBM bytes of each band-pair pass over one step.
 
-    Per band pair each pass streams one grid of N^3 complex values in and one
-    out (16 B per grid point in FP32 complex): pass A reads u_j and writes the
-    codensity transform, pass B reads and writes it, pass C reads it and u_j.
-    Per-target terms are paid once per (target, occupied batch): pass A reads
-    u_a, pass C reads u_a's accumulator and writes it back in FP64 (32 B/pt).
+    Per transformed band pair each pass streams one grid of N^3 complex values
+    in and one out (16 B per grid point in FP32 complex): pass A reads u_j and
+    writes the codensity transform, pass B reads and writes it, pass C reads it
+    and u_j (the role-swapped pass C reads it and u_a).  Per launch and target
+    (per occupied band for the role-swapped pass C): pass A reads u_a, pass C
+    reads the FP64 accumulator and writes it back (32 B/pt).
     """
     n3 = wl.grid[0] ** 3
-    pairs = wl.pair_count()
-    n_jb = -(-wl.n_occ // TJ)            # occupied batches per (k, q, target)
-    per_target = wl.nk * wl.n_tgt * wl.nk * n_jb
-    return {
-        "pass_a": 2 * elem * n3 * pairs + elem * n3 * per_target,
-        "pass_b": 2 * elem * n3 * pairs,
-        "pass_c": 2 * elem * n3 * pairs + 32 * n3 * per_target,
-    }
+    a = b = c = 0
+    for kind, ta, tj in schedule:
+        a += (2 * elem * ta * tj + elem * ta) * n3
+        b += 2 * elem * ta * tj * n3
+        c += (2 * elem * ta * tj + 32 * ta) * n3
+        if kind == "mirrored":
+            c += (2 * elem * ta * tj + 32 * tj) * n3
+    return {"pass_a": a, "pass_b": b, "pass_c": c}
 
 
 def run_oracle_sample(wl, n_occ_sample):
@@ -193,6 +224,24 @@ def profile_case(args):
     from paper_1111_0716_gb300 import synth, xx
     wl = synth.beta_boron()
     prec = xx.XX_FP64 if args.precision == "fp64" else xx.XX_FP32_MIXED
+    if args.profile_shared:
+        # the first two k-points with shared grids: k = q tiles, the pair-symmetric
+        # block (0, 1) (passes A, B, C and the role-swapped pass C at 64 x 80) and
+        # the targets past the occupied set
+        sub = wl.replace(kfrac=wl.kfrac[:2], npw=wl.npw[:2], miller=wl.miller[:2],
+                         coeff=wl.coeff[:2], w=wl.w[:2])
+        plan = xx.Plan.from_workload(sub, precision=prec)
+        c = torch.from_numpy(sub.c_tgt).cuda()
+        ex, vx = plan.energy(c, torch.from_numpy(sub.w_occ).cuda(), c,
+                             torch.from_numpy(sub.w_tgt).cuda(), shared=True)
+        torch.cuda.synchronize()
+        info = plan.info()
+        plan.close()
+        print(json.dumps({"profile_case": sub.name + " (k-points 0, 1)", "pairs": sub.pair_count(),
+                          "transformed": info["pairs_transformed"],
+                          "batch": [info["targets_per_batch"], info["occupied_per_batch"]],
+                          "workspace_gb": info["peak_workspace_bytes"] / 1e9}))
+        return
     plan = xx.Plan.from_workload(wl, precision=prec)
     nt, no = (16, 16) if args.profile_small else (64, 80)
     co = torch.from_numpy(wl.c_occ[:, :no].copy()).cuda()
@@ -260,6 +309,9 @@ def main():
     ap.add_argument("--profile-small", action="store_true",
                     help="with --profile-case: 16 targets x 16 occupied bands (a few GB on the "
                          "device, for multi-pass ncu captures)")
+    ap.add_argument("--profile-shared", action="store_true",
+                    help="with --profile-case: xx_energy on the first two k-points with shared "
+                         "grids (pair-symmetric batches, role-swapped pass C; about 25 GB)")
     ap.add_argument("--with-vjp", action="store_true",
                     help="also time the vector-Jacobian product (xx_apply_vjp, both orbital "
                          "sets) on 16 target bands of every k-point")
@@ -312,6 +364,7 @@ def main():
     plan.profile(True)
     plan.profile_read(reset=True)
     launches0 = plan.info()["kernel_launches"]
+    pairs0 = plan.info()["pairs_transformed"]
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
@@ -327,6 +380,7 @@ def main():
     clk = clocks.stop()
     t = e0.elapsed_time(e1) / 1e3
     launches = plan.info()["kernel_launches"] - launches0
+    pairs_step_transformed = plan.info()["pairs_transformed"] - pairs0
     prof = plan.profile_read(reset=True)
     plan.profile(False)
     info = plan.info()
@@ -375,7 +429,12 @@ def main():
     # device time during the timed steps, against the measured HBM copy rate
     hbm, peak_kind = peaks()
     TA, TJ = info["targets_per_batch"], info["occupied_per_batch"]
-    model = pass_bytes_per_step(wl, TA, TJ)
+    sched = batch_schedule(wl.nk, wl.n_occ, wl.n_tgt, TA, TJ)
+    transformed = sum(ta * tj for _, ta, tj in sched)
+    if transformed * args.steps != pairs_step_transformed:
+        raise RuntimeError("launch schedule model (%d pairs) disagrees with the library (%d)"
+                           % (transformed * args.steps, pairs_step_transformed))
+    model = pass_bytes_per_step(wl, sched)
     dom = max(("pass_a", "pass_b", "pass_c"), key=lambda k: prof[k][0])
     ms_tot, n_l = prof[dom]
     mean_s = ms_tot / 1e3 / max(n_l, 1)
@@ -387,8 +446,8 @@ def main():
                 "traffic": recorded_traffic(dom, [TA, TJ]),
                 "bytes_per_launch": bytes_per_launch, "mean_launch_ms": mean_s * 1e3,
                 "launches": n_l,
-                "path": {"achieved": path_bytes / t / 1e9 / world * world, "frac":
-                         path_bytes / t / 1e9 / hbm, "bytes_per_pair_per_point": 48}}
+                "path": {"achieved": path_bytes / t / 1e9, "frac": path_bytes / t / 1e9 / hbm,
+                         "bytes_per_logical_pair_per_point": path_bytes / args.steps / pairs / (96 ** 3)}}
     shares = {k: v[0] for k, v in prof.items() if v[1]}
     tot = sum(shares.values()) or 1.0
     kernel_share = {k: round(v / tot, 4) for k, v in shares.items()}
@@ -400,8 +459,9 @@ def main():
                        "nk": wl.nk, "n_occ": wl.n_occ, "n_tgt": wl.n_tgt,
                        "pairs_per_step": pairs, "precision": "FP32 FFTs and products, FP64 "
                        "accumulation, kernel table and reductions",
-                       "pairs_counted": "logical (k, a, q, j) applications; on the 8 diagonal "
-                       "k = q blocks each occupied pair is transformed once (W_ja = conj W_aj)",
+                       "pairs_counted": "logical (k, a, q, j) applications; each occupied pair "
+                       "of the blocks (k, q) and (q, k) is transformed once (W_qj,ka = "
+                       "conj W_ka,qj): %d transforms per step" % (pairs_step_transformed // args.steps),
                        "batch": [TA, TJ], "l2": "inputs larger than L2 (orbital grids %.1f GB)"
                        % (wl.nk * wl.n_tgt * 96 ** 3 * 8 / 1e9), "E_x": e_x},
             "e2e": {"value": world * pairs * e2e_steps / t_e2e, "unit": UNIT,

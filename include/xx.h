@@ -91,6 +91,9 @@ typedef struct {
   size_t workspace_bytes;   /* device workspace held now */
   size_t peak_workspace_bytes;
   long long kernel_launches; /* kernels launched by this plan so far */
+  long long pairs_transformed; /* band pairs (or packed slots) that went through the
+                                  codensity transform so far; below the logical pair
+                                  count when the pair symmetry is used */
 } xx_info;
 
 /*
@@ -259,10 +262,19 @@ int xx_apply_vjp(xx_plan plan, const void *c_occ, int ld_occ, const double *w_oc
 int xx_sync(xx_plan plan, void *stream, double timeout_s);
 
 /* Plan options for xx_set_option. */
-#define XX_OPT_PAIR_SYMMETRY 0  /* value != 0 (default): on diagonal blocks k = q, when the
-                                   occupied grids are the leading target grids, transform each
-                                   band pair once and use W_ja = conj(W_aj) for the other
-                                   target (the result differs only by rounding order) */
+#define XX_OPT_PAIR_SYMMETRY 0  /* value != 0 (default): when the occupied grids are the
+                                   leading target grids, transform each occupied band pair
+                                   of a pair of k-points (k, q) once and use W_qj,ka =
+                                   conj(W_ka,qj) for the other target (v depends on |g| only,
+                                   so v(q - k + G) = v(k - q - G)); results differ only by
+                                   rounding order.  On k = q blocks the occupied square is
+                                   cut into tiles and tiles I <= J are transformed.  Of the
+                                   k != q blocks only q > k are transformed: always in the
+                                   pair sums of dE_x/dmu and the strain derivative; in
+                                   xx_apply / xx_energy over all k-points when FP64
+                                   accumulators of every target of every k-point
+                                   (nk * n_tgt * N^3 * 16 bytes) fit in 64 GiB and can be
+                                   allocated, else both orders are transformed */
 #define XX_OPT_REAL_GAMMA 1     /* value != 0: the orbitals passed to later calls are real in
                                    real space (c(-G) = conj c(G) for every G of the basis), so
                                    every codensity is real and, at k = q = Gamma, so is every

@@ -288,6 +288,7 @@ struct xx_plan_s {
       stab, cpack, wpair, acc2;
   size_t ws_bytes = 0, peak_bytes = 0;
   long long launches = 0;
+  long long pairs = 0;          // band pairs (or packed slots) through pass A so far
   // optional per-kernel-class timing with events on the launch stream
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -302,6 +303,9 @@ struct xx_plan_s {
 namespace {
 
 const size_t kDefaultCap = (size_t)16 << 30;
+// FP64 accumulators of every target of every k-point, above which the k != q
+// pair symmetry of xx_apply is not used
+const size_t kCrossAccCap = (size_t)64 << 30;
 const int kGridChunk = 32;   // orbitals per sphere<->grid launch
 
 int cuda_status(cudaError_t e) {
@@ -561,6 +565,62 @@ const char* grid_ptr(xx_plan p, bool shared, int q, int j, int n_occ, int n_tgt)
 int run_apply_real(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, int n_occ,
                    const void* c_tgt, int n_tgt, void* vx_out, cudaStream_t s);
 
+// The band-pair passes of one batch, each bracketed for per-class timing;
+// pass A counts the batch's pairs.
+void run_pass_a(xx_plan p, const PairArgs& a, cudaStream_t s) {
+  const int e = prof_begin(p, s);
+  kset(p).pass_a(a, s);
+  prof_end(p, XX_PROF_PASS_A, e, s);
+  p->pairs += (long long)a.TA * a.TJ;
+}
+
+void run_pass_b(xx_plan p, const PairArgs& a, cudaStream_t s) {
+  const int e = prof_begin(p, s);
+  kset(p).pass_b(a, s);
+  prof_end(p, XX_PROF_PASS_B, e, s);
+}
+
+void run_pass_c(xx_plan p, const PairArgs& a, cudaStream_t s) {
+  const int e = prof_begin(p, s);
+  kset(p).pass_c(a, s);
+  prof_end(p, XX_PROF_PASS_C, e, s);
+}
+
+// role-swapped pass C (profiled with pass C)
+void run_pass_ct(xx_plan p, const PairArgs& a, cudaStream_t s) {
+  const int e = prof_begin(p, s);
+  kset(p).pass_ct(a, s);
+  prof_end(p, XX_PROF_PASS_C, e, s);
+}
+
+// One transformed batch of the pair-symmetric path: targets a0.. (ta of them)
+// of k-point k against occupied bands j0.. (tj) of q.  Pass C adds
+// -(w_qj/N_k) u_qj W_aj into the accumulators of the targets (acc_a); with
+// acc_j set, the role-swapped pass C adds -(w_ka/N_k) u_ka conj(W_aj) into the
+// accumulators of the targets (q, j0..) (W_qj,ka = conj(W_ka,qj)).  The grids
+// are the shared ones of every k-point.
+int sym_batch(xx_plan p, int k, int a0, int ta, int q, int j0, int tj, int n_occ, int n_tgt,
+              const double* w_occ, double2* acc_a, double2* acc_j, cudaStream_t s) {
+  PairArgs a = pair_args(p, ta, tj);
+  a.u_tgt = grid_ptr(p, true, k, a0, n_occ, n_tgt);
+  a.u_occ = grid_ptr(p, true, q, j0, n_occ, n_tgt);
+  a.acc = acc_a;
+  a.w_occ = w_occ + (long long)q * n_occ + j0;
+  run_pass_a(p, a, s);
+  run_pass_b(p, a, s);
+  run_pass_c(p, a, s);
+  int nl = 3;
+  if (acc_j) {
+    PairArgs c = a;
+    c.w_tgt = w_occ + (long long)k * n_occ + a0;
+    c.w_occ = nullptr;
+    c.acc = acc_j;
+    run_pass_ct(p, c, s);
+    ++nl;
+  }
+  return launched(p, nl);
+}
+
 // real: take the real-orbital Gamma path (plan option XX_OPT_REAL_GAMMA)
 int run_apply(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, const double* w_occ,
               int n_occ, const void* c_tgt, int n_tgt, void* vx_out, bool real, cudaStream_t s) {
@@ -574,79 +634,79 @@ int run_apply(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, const do
   p->tj_last = TJ;
   const size_t eb = elem_bytes(p);
   if ((st = ensure(p, p->inter, (size_t)TA * TJ * p->N * P(p, 1) * P(p, 0) * eb))) return st;
-  if ((st = ensure(p, p->acc, (size_t)n_tgt * n3(p) * 16))) return st;
-  const KernelSet& ks = kset(p);
-  // k = q pair symmetry: with the occupied grids shared with the leading
-  // targets, W_ja = conj(W_aj) on the diagonal block (v(G) = v(-G) there), so the
-  // occupied square is tiled and only tiles I <= J are transformed.
+  // Pair symmetry: with the occupied grids shared with the leading targets,
+  // W_qj,ka = conj(W_ka,qj) (v(q - k + G) = v(k - q - G)).  On k = q blocks the
+  // occupied square is tiled and only tiles I <= J are transformed; across
+  // k-points (cross) only blocks q > k are, which needs the accumulators of
+  // every k-point at once.
   const bool sym = shared && p->pair_symmetry && n_occ > 1;
+  const size_t acc_k_bytes = (size_t)n_tgt * n3(p) * 16;
+  bool cross = sym && p->nk > 1 && (size_t)p->nk * acc_k_bytes <= kCrossAccCap;
+  if (cross) {
+    st = ensure(p, p->acc, (size_t)p->nk * acc_k_bytes);
+    if (st == XX_ERR_OUT_OF_MEMORY)
+      cross = false;
+    else if (st)
+      return st;
+  }
+  if (!cross && (st = ensure(p, p->acc, acc_k_bytes))) return st;
+  const long long acc_k_elems = (long long)n_tgt * n3(p);
+  if (cross) cudaMemsetAsync(p->acc.p, 0, (size_t)p->nk * acc_k_bytes, s);
   const int T = TJ < TA ? TJ : TA;
   for (int kk = 0; kk < kn; ++kk) {
     const int k = k0 + kk;
-    cudaMemsetAsync(p->acc.p, 0, (size_t)n_tgt * n3(p) * 16, s);
+    double2* acc_k = (double2*)p->acc.p + (cross ? k * acc_k_elems : 0);
+    if (!cross) cudaMemsetAsync(acc_k, 0, acc_k_bytes, s);
     for (int q = 0; q < p->nk; ++q) {
-      if ((st = kernel_table_for(p, k, q, false, s))) return st;
       const bool diag = sym && q == k;
+      const bool upper = cross && q > k;   // occupied square, both directions
+      const bool lower = cross && q < k;   // occupied square done by block (q, k)
+      const int a_first = (diag || upper || lower) ? n_occ : 0;
+      if (lower && a_first >= n_tgt) continue;
+      if ((st = kernel_table_for(p, k, q, false, s))) return st;
       if (diag) {
         for (int i0 = 0; i0 < n_occ; i0 += T) {
           const int ti = (n_occ - i0) < T ? (n_occ - i0) : T;
           for (int j0 = i0; j0 < n_occ; j0 += T) {
             const int tj = (n_occ - j0) < T ? (n_occ - j0) : T;
-            PairArgs a = pair_args(p, ti, tj);
-            a.u_tgt = grid_ptr(p, true, kk, i0, n_occ, n_tgt);
-            a.u_occ = grid_ptr(p, true, q, j0, n_occ, n_tgt);
-            a.acc = (double2*)p->acc.p + (long long)i0 * n3(p);
-            a.w_occ = w_occ + (long long)q * n_occ + j0;
-            int e = prof_begin(p, s);
-            ks.pass_a(a, s);
-            prof_end(p, XX_PROF_PASS_A, e, s);
-            e = prof_begin(p, s);
-            ks.pass_b(a, s);
-            prof_end(p, XX_PROF_PASS_B, e, s);
-            e = prof_begin(p, s);
-            ks.pass_c(a, s);
-            prof_end(p, XX_PROF_PASS_C, e, s);
-            int nl = 3;
-            if (j0 > i0) {
-              // targets of tile J receive -(w_a/N_k) u_a conj(W_aj) from tile I
-              PairArgs c = a;
-              c.u_tgt = grid_ptr(p, true, kk, i0, n_occ, n_tgt);
-              c.w_tgt = w_occ + (long long)k * n_occ + i0;
-              c.w_occ = nullptr;
-              c.acc = (double2*)p->acc.p + (long long)j0 * n3(p);
-              e = prof_begin(p, s);
-              ks.pass_ct(c, s);
-              prof_end(p, XX_PROF_PASS_C, e, s);
-              ++nl;
-            }
-            if ((st = launched(p, nl))) return st;
+            // tiles J > I: targets of tile J receive -(w_a/N_k) u_a conj(W_aj)
+            st = sym_batch(p, k, i0, ti, q, j0, tj, n_occ, n_tgt, w_occ, acc_k + (long long)i0 * n3(p),
+                           j0 > i0 ? acc_k + (long long)j0 * n3(p) : nullptr, s);
+            if (st) return st;
           }
         }
       }
-      for (int a0 = diag ? n_occ : 0; a0 < n_tgt; a0 += TA) {
+      if (upper) {
+        double2* acc_q = (double2*)p->acc.p + q * acc_k_elems;
+        for (int a0 = 0; a0 < n_occ; a0 += TA) {
+          const int ta = (n_occ - a0) < TA ? (n_occ - a0) : TA;
+          for (int j0 = 0; j0 < n_occ; j0 += TJ) {
+            const int tj = (n_occ - j0) < TJ ? (n_occ - j0) : TJ;
+            st = sym_batch(p, k, a0, ta, q, j0, tj, n_occ, n_tgt, w_occ,
+                           acc_k + (long long)a0 * n3(p), acc_q + (long long)j0 * n3(p), s);
+            if (st) return st;
+          }
+        }
+      }
+      for (int a0 = a_first; a0 < n_tgt; a0 += TA) {
         const int ta = (n_tgt - a0) < TA ? (n_tgt - a0) : TA;
         for (int j0 = 0; j0 < n_occ; j0 += TJ) {
           const int tj = (n_occ - j0) < TJ ? (n_occ - j0) : TJ;
           PairArgs a = pair_args(p, ta, tj);
           a.u_tgt = grid_ptr(p, true, kk, a0, n_occ, n_tgt);
           a.u_occ = grid_ptr(p, shared, q, j0, n_occ, n_tgt);
-          a.acc = (double2*)p->acc.p + (long long)a0 * n3(p);
+          a.acc = acc_k + (long long)a0 * n3(p);
           a.w_occ = w_occ + (long long)q * n_occ + j0;
-          int e = prof_begin(p, s);
-          ks.pass_a(a, s);
-          prof_end(p, XX_PROF_PASS_A, e, s);
-          e = prof_begin(p, s);
-          ks.pass_b(a, s);
-          prof_end(p, XX_PROF_PASS_B, e, s);
-          e = prof_begin(p, s);
-          ks.pass_c(a, s);
-          prof_end(p, XX_PROF_PASS_C, e, s);
+          run_pass_a(p, a, s);
+          run_pass_b(p, a, s);
+          run_pass_c(p, a, s);
           if ((st = launched(p, 3))) return st;
         }
       }
     }
-    st = grid_to_sphere(p, k, (const double2*)p->acc.p, n_tgt,
-                        (double2*)vx_out + (long long)kk * n_tgt * p->npw_max, s);
+    // every contribution to the targets of k is in: blocks (k', k) with k' < k
+    // ran in earlier iterations
+    st = grid_to_sphere(p, k, acc_k, n_tgt, (double2*)vx_out + (long long)kk * n_tgt * p->npw_max, s);
     if (st) return st;
   }
   return XX_OK;
@@ -746,13 +806,9 @@ int run_apply_real(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ
     a.u_occ = (const char*)p->u_occ.p + (size_t)s0 * nn * eb;
     a.acc = (double2*)p->acc.p + (long long)a0 * nn;
     a.w_pair = (const double2*)p->wpair.p + s0;
+    run_pass_a(p, a, s);
+    run_pass_b(p, a, s);
     int e = prof_begin(p, s);
-    ks.pass_a(a, s);
-    prof_end(p, XX_PROF_PASS_A, e, s);
-    e = prof_begin(p, s);
-    ks.pass_b(a, s);
-    prof_end(p, XX_PROF_PASS_B, e, s);
-    e = prof_begin(p, s);
     ks.pass_c_packed(a, s);
     prof_end(p, XX_PROF_PASS_C, e, s);
     if (!mirrored) return launched(p, 3);
@@ -762,9 +818,7 @@ int run_apply_real(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ
     c.w_tgt = w_occ + a0;
     c.w_occ = nullptr;
     c.acc = (double2*)p->acc2.p + (long long)s0 * nn;
-    e = prof_begin(p, s);
-    ks.pass_ct(c, s);
-    prof_end(p, XX_PROF_PASS_C, e, s);
+    run_pass_ct(p, c, s);
     return launched(p, 4);
   });
   if (st) return st;
@@ -803,7 +857,7 @@ int run_pair_sums_real(xx_plan p, const void* c, const double* w, int n_b, bool 
     a.u_tgt = (const char*)p->u_tgt.p + (size_t)a0 * nn * eb;
     a.u_occ = (const char*)p->u_occ.p + (size_t)s0 * nn * eb;
     const double scale = mirrored ? 2.0 : 1.0;
-    ks.pass_a(a, s);
+    run_pass_a(p, a, s);
     if (strain) {
       a.dvt = p->stab.p;
       ks.pass_b_strain(a, s);
@@ -854,26 +908,28 @@ int run_dmu(xx_plan p, const void* c, const double* w, int n_b, double grad, dou
   if ((st = ensure(p, p->dmu_acc, 8))) return st;
   cudaMemsetAsync(p->dmu_acc.p, 0, 8, s);
   const KernelSet& ks = kset(p);
-  // on diagonal blocks k = q, |rhohat_ja| = |rhohat_aj|: tiles I < J count twice,
-  // tiles J < I are skipped (square tiles, option XX_OPT_PAIR_SYMMETRY)
+  // pair symmetry (option XX_OPT_PAIR_SYMMETRY): the pair sum of (qj, ka) equals
+  // that of (ka, qj) (|rhohat_qj,ka(G)| = |rhohat_ka,qj(-G)|, v'(q - k + G) =
+  // v'(k - q - G)), so blocks q < k are skipped and blocks q > k count twice; on
+  // k = q blocks tiles I < J count twice and tiles J < I are skipped
   const int T = TJ < TA ? TJ : TA;
   for (int k = 0; k < p->nk; ++k)
     for (int q = 0; q < p->nk; ++q) {
+      if (p->pair_symmetry && q < k) continue;
       if ((st = kernel_table_for(p, k, q, true, s))) return st;
       const bool diag = p->pair_symmetry && q == k && n_b > 1;
+      const double block_scale = (p->pair_symmetry && q > k) ? 2.0 : 1.0;
       const int SA = diag ? T : TA, SJ = diag ? T : TJ;
       for (int a0 = 0; a0 < n_b; a0 += SA) {
         const int ta = (n_b - a0) < SA ? (n_b - a0) : SA;
         for (int j0 = diag ? a0 : 0; j0 < n_b; j0 += SJ) {
           const int tj = (n_b - j0) < SJ ? (n_b - j0) : SJ;
-          const double scale = (diag && j0 > a0) ? 2.0 : 1.0;
+          const double scale = (diag && j0 > a0) ? 2.0 : block_scale;
           PairArgs a = pair_args(p, ta, tj);
           a.u_tgt = grid_ptr(p, true, k, a0, n_b, n_b);
           a.u_occ = grid_ptr(p, true, q, j0, n_b, n_b);
+          run_pass_a(p, a, s);
           int e = prof_begin(p, s);
-          ks.pass_a(a, s);
-          prof_end(p, XX_PROF_PASS_A, e, s);
-          e = prof_begin(p, s);
           ks.pass_b_dmu(a, s);
           prof_end(p, XX_PROF_PASS_B_DMU, e, s);
           k_dmu_batch<<<1, kRedThreads, 0, s>>>((const double*)p->partial.p, P(p, 1), ta, tj,
@@ -937,21 +993,24 @@ int run_strain(xx_plan p, const void* c, const double* w, int n_b, double* out9,
   if ((st = ensure(p, p->partial, (size_t)TA * TJ * P(p, 1) * 7 * 8))) return st;
   const KernelSet& ks = kset(p);
   const int T = TJ < TA ? TJ : TA;
+  // pair symmetry as in the dE/dmu sums (g_a g_b is even in g)
   for (int k = 0; k < p->nk; ++k)
     for (int q = 0; q < p->nk; ++q) {
+      if (p->pair_symmetry && q < k) continue;
       if ((st = strain_tables(p, k, q, s))) return st;
       const bool diag = p->pair_symmetry && q == k && n_b > 1;
+      const double block_scale = (p->pair_symmetry && q > k) ? 2.0 : 1.0;
       const int SA = diag ? T : TA, SJ = diag ? T : TJ;
       for (int a0 = 0; a0 < n_b; a0 += SA) {
         const int ta = (n_b - a0) < SA ? (n_b - a0) : SA;
         for (int j0 = diag ? a0 : 0; j0 < n_b; j0 += SJ) {
           const int tj = (n_b - j0) < SJ ? (n_b - j0) : SJ;
-          const double scale = (diag && j0 > a0) ? 2.0 : 1.0;
+          const double scale = (diag && j0 > a0) ? 2.0 : block_scale;
           PairArgs a = pair_args(p, ta, tj);
           a.u_tgt = grid_ptr(p, true, k, a0, n_b, n_b);
           a.u_occ = grid_ptr(p, true, q, j0, n_b, n_b);
           a.dvt = p->stab.p;
-          ks.pass_a(a, s);
+          run_pass_a(p, a, s);
           ks.pass_b_strain(a, s);
           k_strain_batch<<<1, kRedThreads, 0, s>>>((const double*)p->partial.p, P(p, 1), ta, tj,
                                                    w + (long long)k * n_b + a0,
@@ -1003,12 +1062,12 @@ int run_vjp_occ(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, i
           a.w_occ = w_occ + (long long)q * n_occ + j0;
           // term 1: W_aj from (u_a, u_j), multiplied by ubar_a
           a.u_tgt = ut;
-          ks.pass_a(a, s);
+          run_pass_a(p, a, s);
           ks.pass_b(a, s);
           a.u_tgt = ub;
           ks.pass_ct(a, s);
           // term 2: Wbar_aj from (ubar_a, u_j), multiplied by u_a
-          ks.pass_a(a, s);
+          run_pass_a(p, a, s);
           ks.pass_b(a, s);
           a.u_tgt = ut;
           ks.pass_ct(a, s);
@@ -1484,6 +1543,7 @@ int xx_plan_info(xx_plan p, xx_info* info) {
   info->workspace_bytes = p->ws_bytes;
   info->peak_workspace_bytes = p->peak_bytes;
   info->kernel_launches = p->launches;
+  info->pairs_transformed = p->pairs;
   return XX_OK;
 }
 

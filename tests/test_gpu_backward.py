@@ -124,10 +124,19 @@ def test_sync_time_limit_reports_timeout_without_cancelling(gpu):
     plan.close()
 
 
+def rhombo_mesh():
+    """Rhombohedral cell with a 2x2x2 MP mesh (8 k-points, 4 bands)."""
+    return synth.make_workload("rhombo24", synth.rhombohedral_lattice(7.5, 65.0), (24,) * 3,
+                               synth.monkhorst_pack(2), 2.4, 4, 4, [1.0, 1.0, 0.75, 0.3], 21)
+
+
+@pytest.mark.parametrize("make", [lambda: synth.sweep_cell(0), rhombo_mesh])
 @pytest.mark.parametrize("prec,tol", [(0, gu.FP32_TOL), (1, 1e-12)])
-def test_dmu_pair_symmetry_matches_direct_pairs(gpu, prec, tol):
+def test_dmu_pair_symmetry_matches_direct_pairs(gpu, prec, tol, make):
+    """dE/dmu with the pair symmetry (k = q tiles, blocks q > k counted twice) and
+    with every pair transformed."""
     torch, xx = gpu
-    wl = synth.sweep_cell(0)
+    wl = make()
     out = []
     for on in (True, False):
         plan = xx.Plan.from_workload(wl, precision=prec)

@@ -212,7 +212,8 @@ def test_run_many_sweep_cells_match_single_runs(gpu):
                                            (lambda: synth.sweep_cell(1), 1, 1e-12),
                                            (lambda: rhombo24(), 1, 1e-12)])
 def test_pair_symmetry_matches_direct_pairs(gpu, make, prec, tol):
-    """k = q pair symmetry (default) against transforming every pair (option off)."""
+    """Pair symmetry (default; k = q tiles and, on k-meshes, blocks q > k) against
+    transforming every pair (option off)."""
     torch, xx = gpu
     wl = make()
     out = []
@@ -227,3 +228,33 @@ def test_pair_symmetry_matches_direct_pairs(gpu, make, prec, tol):
         plan.close()
     assert gu.rel_max(out[0][0], out[1][0]) <= tol
     assert abs(out[0][1] - out[1][1]) <= tol * abs(out[1][1])
+
+
+def expected_transforms(nk, n_occ, n_tgt, TA, TJ, sym):
+    """Band pairs the host loop sends through the codensity transform."""
+    if not sym:
+        return nk * nk * n_tgt * n_occ
+    T = min(TA, TJ)
+    tiles = [min(T, n_occ - i) for i in range(0, n_occ, T)]
+    diag = sum(tiles[i] * tiles[j] for i in range(len(tiles)) for j in range(i, len(tiles)))
+    rest = (n_tgt - n_occ) * n_occ            # targets past the occupied set meet every j
+    upper = nk * (nk - 1) // 2                # blocks q > k: the whole occupied square
+    return nk * (diag + rest) + upper * (n_occ * n_occ + rest) + (nk * nk - nk - upper) * rest
+
+
+def test_pair_symmetry_transform_count(gpu):
+    """The k != q symmetry transforms each occupied pair of blocks (k, q), (q, k) once."""
+    torch, xx = gpu
+    wl = rhombo24()
+    logical = wl.nk * wl.n_tgt * wl.nk * wl.n_occ
+    for on in (True, False):
+        plan = xx.Plan.from_workload(wl, precision=0)
+        plan.set_batch(3, 3)
+        plan.set_pair_symmetry(on)
+        c = gu.dev(wl.c_tgt)
+        plan.energy(c, gu.dev(wl.w_occ), c, gu.dev(wl.w_tgt), shared=True)
+        plan.sync(timeout_s=600.0)
+        n = plan.info()["pairs_transformed"]
+        plan.close()
+        assert n == expected_transforms(wl.nk, wl.n_occ, wl.n_tgt, 3, 3, on)
+    assert expected_transforms(wl.nk, wl.n_occ, wl.n_tgt, 3, 3, True) < logical

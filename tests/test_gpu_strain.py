@@ -60,10 +60,12 @@ def test_strain_derivative_matches_finite_differences(gpu, oracle_mod, kernel):
     assert abs(e32 - e64) <= gu.FP32_TOL * abs(e64)
 
 
-def test_strain_derivative_pair_symmetry(gpu):
-    """The k = q pair symmetry (default) and transforming every pair agree (FP64)."""
+@pytest.mark.parametrize("make", [synth.tiny_cubic, lambda: rhombo16(synth.KERNEL_HSE)])
+def test_strain_derivative_pair_symmetry(gpu, make):
+    """The pair symmetry (default: k = q tiles, blocks q > k counted twice) and
+    transforming every pair agree (FP64)."""
     torch, xx = gpu
-    wl = synth.tiny_cubic()
+    wl = make()
     res = []
     for on in (True, False):
         plan = xx.Plan.from_workload(wl, precision=1)
