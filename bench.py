@@ -17,6 +17,8 @@ Printed as one JSON line (rank 0):
   fp64_slice    the all-FP64 GPU path on a slice of the same workload
   real_gamma    the real-orbital Gamma path against the general path on the same
                 cell at the Gamma point only (real orbitals, 30,720 pairs)
+  exact_grid    the same workload with the plan on the smallest grid on which the
+                operator is exact (60^3; same V_x c and E_x up to rounding)
   --impl reference  times the oracle as the reference arm.
 Multi-GPU (torchrun): each rank runs an independent workload (its own seed),
 weak scaling; value = all ranks' pairs / max-over-ranks time.
@@ -289,6 +291,34 @@ def real_gamma_leg(xx, torch, stream, reps=3):
                       % (wl.name, wl.n_occ, wl.n_tgt, pairs, reps)}
 
 
+def exact_grid_leg(xx, torch, wl, stream, e_ref, reps=2):
+    """The same workload on the smallest grid on which the operator is exact
+    (N >= 4 n_max + 1: 60^3 for this basis), through the same xx_energy call."""
+    n = xx.xx_exact_grid(wl.n_max())
+    small = wl.replace(grid=(n,) * 3)
+    plan = xx.Plan.from_workload(small, precision=xx.XX_FP32_MIXED)
+    c = torch.from_numpy(small.c_tgt).cuda()
+    wo = torch.from_numpy(small.w_occ).cuda()
+    wt = torch.from_numpy(small.w_tgt).cuda()
+    ex, vx = plan.energy(c, wo, c, wt, shared=True, stream=stream)
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(reps):
+        plan.energy(c, wo, c, wt, vx_out=vx, ex_out=ex, shared=True, stream=stream)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    plan.sync(timeout_s=60.0, stream=stream)
+    t = g0.elapsed_time(g1) / 1e3 / reps
+    e = float(ex[0].item())
+    plan.close()
+    return {"value": wl.pair_count() / t, "unit": UNIT, "grid": n,
+            "E_x_rel_diff_vs_%d" % wl.grid[0]: abs(e - e_ref) / abs(e_ref),
+            "sample": "%s with the plan created on the %d^3 grid (4 n_max + 1 = %d), FP32-mixed, "
+                      "mean of %d steps" % (wl.name, n, 4 * int(wl.n_max().max()) + 1, reps)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -301,6 +331,8 @@ def main():
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 slice")
     ap.add_argument("--no-real", action="store_true", help="skip the real-orbital Gamma leg")
+    ap.add_argument("--no-exact-grid", action="store_true",
+                    help="skip the smallest-exact-grid leg")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one small slice of the workload (k=0, 16 targets, 32 occupied "
                          "bands, all q) once and exit: the case ncu captures")
@@ -508,6 +540,9 @@ def main():
 
     if rank == 0 and not args.no_real:
         line["real_gamma"] = real_gamma_leg(xx, torch, stream)
+
+    if rank == 0 and not args.no_exact_grid:
+        line["exact_grid"] = exact_grid_leg(xx, torch, wl, stream, e_x)
 
     if rank == 0 and args.with_vjp:
         nt = 16

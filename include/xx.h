@@ -290,6 +290,15 @@ int xx_sync(xx_plan plan, void *stream, double timeout_s);
                                    XX_ERR_INVALID_ARGUMENT); with complex orbitals the results
                                    are wrong.  Default 0. */
 
+#define XX_OPT_TMA_PASS_B 2     /* FP32 pass B (the z transforms and kernel multiply of the
+                                   band-pair intermediates): 1 (default) runs the
+                                   persistent kernel whose rows arrive by bulk tensor copies,
+                                   two rows ahead, when the kept f_x of a row are at most
+                                   3/4 of the grid length, else the one-row-per-block
+                                   kernel; 2 always the tensor-copy kernel; 0 never.  Both
+                                   run the same arithmetic in the same order.  Other values
+                                   give XX_ERR_INVALID_ARGUMENT. */
+
 /* Set a plan option; XX_ERR_INVALID_ARGUMENT for an unknown option. */
 int xx_set_option(xx_plan plan, int option, long long value);
 
@@ -320,6 +329,20 @@ int xx_profile_read(xx_plan plan, double *ms, long long *launches, int n_classes
 
 /* Fill *info with the plan's facts. */
 int xx_plan_info(xx_plan plan, xx_info *info);
+
+/*
+ * Smallest FFT grid length this library supports on which the operator is
+ * exact (the no-wrap-around condition of the setup section, read as
+ * N >= 4 n_max + 1 on every axis): n_max[3] is the largest |Miller index| of
+ * the basis sets per axis (host array), *n_out receives the cubic length.  On
+ * such a grid every codensity transform is exact on its support |f| <= 2 n_max
+ * and the sphere projection of u_j W sees no alias, so V_x c, E_x and the
+ * gradients equal those computed on any larger admissible grid up to rounding.
+ * Host only (no GPU work).  Returns XX_ERR_INVALID_ARGUMENT (NULL pointer,
+ * negative n_max), XX_ERR_UNSUPPORTED_GRID (no supported length is large
+ * enough) or XX_OK.
+ */
+int xx_exact_grid(const int *n_max, int *n_out);
 
 /*
  * E_x reduction for callers that cannot allocate device memory.  The paper has

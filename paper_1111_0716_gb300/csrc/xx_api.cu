@@ -9,6 +9,10 @@
 //     for q: kernel table v(k - q + G)
 //       for each (target batch, occupied batch): pass A, pass B, pass C
 //     grid -> sphere of the accumulators into V_x c
+// (with the pair symmetry, blocks q > k also feed the targets of q, and the
+// accumulators of every k-point are zeroed once up front)
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -275,6 +279,9 @@ struct xx_plan_s {
   size_t cap = 0;
   int ta_user = 0, tj_user = 0;
   bool pair_symmetry = true;
+  int tma_pass_b = 1;          // XX_OPT_TMA_PASS_B: 0 off, 1 when pruning keeps <= 3/4 of a row, 2 always
+  int sm_count = 0;
+  int tma_per_sm = -1;         // resident tensor-copy pass B CTAs per SM (-1: not queried)
   bool real_gamma = false;     // XX_OPT_REAL_GAMMA
   bool gamma_closed = false;   // one k-point at Gamma whose basis holds -G for every G
   int ta_last = 0, tj_last = 0;
@@ -349,6 +356,16 @@ long long n3(const xx_plan p) { return (long long)p->N * p->N * p->N; }
 
 int P(const xx_plan p, int ax) { return 2 * p->h[ax] + 1; }
 int Q(const xx_plan p, int ax) { return 2 * p->nmax[ax] + 1; }
+
+// Row pitch of the pair intermediates: the P1 kept f_x, rounded up to an even
+// count in FP32 so that every row is a whole number of 16-byte units (the
+// tensor-copy rule of pass B).
+int LX(const xx_plan p) { return p->prec == XX_FP64 ? P(p, 0) : (P(p, 0) + 1) & ~1; }
+
+// bytes of one band pair's intermediate, [N][P2][LX]
+size_t inter_pair_bytes(const xx_plan p) {
+  return (size_t)p->N * P(p, 1) * LX(p) * (p->prec == XX_FP64 ? 16 : 8);
+}
 
 const KernelSet& kset(const xx_plan p) { return p->prec == XX_FP64 ? p->kt->f64 : p->kt->f32; }
 
@@ -496,7 +513,7 @@ int kernel_table_for(xx_plan p, int k, int q, bool with_dmu, cudaStream_t s) {
 }
 
 void batch_shape(xx_plan p, int n_tgt, int n_occ, int* TA, int* TJ) {
-  const size_t per_pair = (size_t)p->N * P(p, 1) * P(p, 0) * elem_bytes(p);
+  const size_t per_pair = inter_pair_bytes(p);
   // 64 x 80 measured best on the 96^3 workload: a long occupied loop amortises
   // pass C's prologue and FP64 accumulator update, and 6144 CTAs per launch
   // keep the last wave short
@@ -527,7 +544,9 @@ PairArgs pair_args(xx_plan p, int TA, int TJ) {
   a.P1 = P(p, 0);
   a.P2 = P(p, 1);
   a.P3 = P(p, 2);
+  a.LX = LX(p);
   a.coef = -1.0 / (double)p->nk;
+  a.err = p->d_err;
   return a;
 }
 
@@ -574,9 +593,57 @@ void run_pass_a(xx_plan p, const PairArgs& a, cudaStream_t s) {
   p->pairs += (long long)a.TA * a.TJ;
 }
 
+// cuTensorMapEncodeTiled from the driver, resolved once (nullptr if unavailable)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+
+// Pass B of one batch.  FP32 takes the tensor-copy staged kernel: the
+// intermediates viewed as floats [N * pairs][P2][2 LX], one box of 2 LX x 1 x N
+// (a row's N z-planes) per item; a row is 8 LX bytes (a multiple of 16, LX even).
 void run_pass_b(xx_plan p, const PairArgs& a, cudaStream_t s) {
   const int e = prof_begin(p, s);
-  kset(p).pass_b(a, s);
+  bool done = false;
+  // measured on GB300 (beta cell, 64 targets x 160 occupied x 8 q): P1 = 57 of N = 96,
+  // tensor-copy kernel 4.5 % faster than the row kernel; P1 = 57 of N = 60, 14 % slower
+  const bool want = p->tma_pass_b == 2 || (p->tma_pass_b == 1 && 4 * a.P1 <= 3 * p->N);
+  PFN_cuTensorMapEncodeTiled_v12000 enc = p->prec == XX_FP32_MIXED && want ? tensor_map_encoder() : nullptr;
+  if (enc && 2 * a.LX <= 256 && p->N <= 256) {
+    if (p->tma_per_sm < 0) {
+      p->tma_per_sm = p->kt->pass_b_tma_per_sm(a.LX, a.P1, a.P3);
+      if (cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+        cudaGetLastError();
+        p->tma_per_sm = 0;
+      }
+    }
+    if (p->tma_per_sm > 0) {
+      const cuuint64_t dims[3] = {(cuuint64_t)(2 * a.LX), (cuuint64_t)a.P2, (cuuint64_t)p->N * a.TA * a.TJ};
+      const cuuint64_t strides[2] = {(cuuint64_t)a.LX * 8, (cuuint64_t)a.P2 * a.LX * 8};
+      const cuuint32_t box[3] = {(cuuint32_t)(2 * a.LX), 1, (cuuint32_t)p->N};
+      const cuuint32_t estr[3] = {1, 1, 1};
+      CUtensorMap tm;
+      if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.inter, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+        const long long items = (long long)a.P2 * a.TA * a.TJ;
+        const long long slots = (long long)p->sm_count * p->tma_per_sm;
+        p->kt->pass_b_tma(a, tm, (int)(items < slots ? items : slots), s);
+        done = true;
+      }
+    }
+  }
+  if (!done) kset(p).pass_b(a, s);
   prof_end(p, XX_PROF_PASS_B, e, s);
 }
 
@@ -633,7 +700,7 @@ int run_apply(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, const do
   p->ta_last = TA;
   p->tj_last = TJ;
   const size_t eb = elem_bytes(p);
-  if ((st = ensure(p, p->inter, (size_t)TA * TJ * p->N * P(p, 1) * P(p, 0) * eb))) return st;
+  if ((st = ensure(p, p->inter, (size_t)TA * TJ * inter_pair_bytes(p)))) return st;
   // Pair symmetry: with the occupied grids shared with the leading targets,
   // W_qj,ka = conj(W_ka,qj) (v(q - k + G) = v(k - q - G)).  On k = q blocks the
   // occupied square is tiled and only tiles I <= J are transformed; across
@@ -791,7 +858,7 @@ int run_apply_real(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ
   const int T = real_tile(TA, TJ);
   long long npair = (long long)TA * TJ;
   if (sym && (long long)T * (T / 2) > npair) npair = (long long)T * (T / 2);
-  if ((st = ensure(p, p->inter, (size_t)npair * p->N * P(p, 1) * P(p, 0) * eb))) return st;
+  if ((st = ensure(p, p->inter, (size_t)npair * inter_pair_bytes(p)))) return st;
   if ((st = ensure(p, p->acc, (size_t)n_tgt * nn * 16))) return st;
   cudaMemsetAsync(p->acc.p, 0, (size_t)n_tgt * nn * 16, s);
   if (sym) {
@@ -849,7 +916,7 @@ int run_pair_sums_real(xx_plan p, const void* c, const double* w, int n_b, bool 
   long long npair = (long long)TA * TJ;
   if (sym && (long long)T * (T / 2) > npair) npair = (long long)T * (T / 2);
   const int nsum = strain ? 7 : 1;
-  if ((st = ensure(p, p->inter, (size_t)npair * p->N * P(p, 1) * P(p, 0) * eb))) return st;
+  if ((st = ensure(p, p->inter, (size_t)npair * inter_pair_bytes(p)))) return st;
   if ((st = ensure(p, p->partial, (size_t)npair * P(p, 1) * nsum * 8))) return st;
   const KernelSet& ks = kset(p);
   return for_real_tiles(n_b, n_b, TA, TJ, sym, T, [&](int a0, int ta, int s0, int ns, bool mirrored) {
@@ -903,7 +970,7 @@ int run_dmu(xx_plan p, const void* c, const double* w, int n_b, double grad, dou
   int TA, TJ;
   batch_shape(p, n_b, n_b, &TA, &TJ);
   const size_t eb = elem_bytes(p);
-  if ((st = ensure(p, p->inter, (size_t)TA * TJ * p->N * P(p, 1) * P(p, 0) * eb))) return st;
+  if ((st = ensure(p, p->inter, (size_t)TA * TJ * inter_pair_bytes(p)))) return st;
   if ((st = ensure(p, p->partial, (size_t)TA * TJ * P(p, 1) * 8))) return st;
   if ((st = ensure(p, p->dmu_acc, 8))) return st;
   cudaMemsetAsync(p->dmu_acc.p, 0, 8, s);
@@ -989,7 +1056,7 @@ int run_strain(xx_plan p, const void* c, const double* w, int n_b, double* out9,
   int TA, TJ;
   batch_shape(p, n_b, n_b, &TA, &TJ);
   const size_t eb = elem_bytes(p);
-  if ((st = ensure(p, p->inter, (size_t)TA * TJ * p->N * P(p, 1) * P(p, 0) * eb))) return st;
+  if ((st = ensure(p, p->inter, (size_t)TA * TJ * inter_pair_bytes(p)))) return st;
   if ((st = ensure(p, p->partial, (size_t)TA * TJ * P(p, 1) * 7 * 8))) return st;
   const KernelSet& ks = kset(p);
   const int T = TJ < TA ? TJ : TA;
@@ -1043,7 +1110,7 @@ int run_vjp_occ(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, i
   }
   int TA, TJ;
   batch_shape(p, n_tgt, n_occ, &TA, &TJ);
-  if ((st = ensure(p, p->inter, (size_t)TA * TJ * p->N * P(p, 1) * P(p, 0) * eb))) return st;
+  if ((st = ensure(p, p->inter, (size_t)TA * TJ * inter_pair_bytes(p)))) return st;
   if ((st = ensure(p, p->acc, (size_t)n_occ * n3(p) * 16))) return st;
   const KernelSet& ks = kset(p);
   for (int q = 0; q < p->nk; ++q) {
@@ -1063,12 +1130,12 @@ int run_vjp_occ(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, i
           // term 1: W_aj from (u_a, u_j), multiplied by ubar_a
           a.u_tgt = ut;
           run_pass_a(p, a, s);
-          ks.pass_b(a, s);
+          run_pass_b(p, a, s);
           a.u_tgt = ub;
           ks.pass_ct(a, s);
           // term 2: Wbar_aj from (ubar_a, u_j), multiplied by u_a
           run_pass_a(p, a, s);
-          ks.pass_b(a, s);
+          run_pass_b(p, a, s);
           a.u_tgt = ut;
           ks.pass_ct(a, s);
           if ((st = launched(p, 6))) return st;
@@ -1485,6 +1552,10 @@ int xx_set_option(xx_plan p, int option, long long value) {
       if (value != 0 && !p->gamma_closed) return XX_ERR_INVALID_ARGUMENT;
       p->real_gamma = value != 0;
       return XX_OK;
+    case XX_OPT_TMA_PASS_B:
+      if (value < 0 || value > 2) return XX_ERR_INVALID_ARGUMENT;
+      p->tma_pass_b = (int)value;
+      return XX_OK;
     default:
       return XX_ERR_INVALID_ARGUMENT;
   }
@@ -1524,6 +1595,22 @@ int xx_profile_read(xx_plan p, double* ms, long long* launches, int n_classes, i
     p->ev_next = 0;
   }
   return XX_OK;
+}
+
+int xx_exact_grid(const int* n_max, int* n_out) {
+  if (!n_max || !n_out) return XX_ERR_INVALID_ARGUMENT;
+  int need = 0;
+  for (int ax = 0; ax < 3; ++ax) {
+    if (n_max[ax] < 0 || n_max[ax] > 4096) return XX_ERR_INVALID_ARGUMENT;
+    const int m = 4 * n_max[ax] + 1;
+    if (m > need) need = m;
+  }
+  for (int n = need; n <= 96; ++n)
+    if (supported_n(n)) {
+      *n_out = n;
+      return XX_OK;
+    }
+  return XX_ERR_UNSUPPORTED_GRID;
 }
 
 int xx_plan_info(xx_plan p, xx_info* info) {

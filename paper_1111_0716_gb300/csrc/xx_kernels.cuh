@@ -18,6 +18,8 @@
 // and fixed-order reductions for E_x and dE_x/dmu.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the tensor map itself is encoded on the host)
+
 #include "xx_fft.cuh"
 
 namespace xx {
@@ -27,7 +29,7 @@ namespace xx {
 struct PairArgs {
   const void* u_tgt;     // [TA][N^3] grids of the target batch (at k)
   const void* u_occ;     // [TJ][N^3] grids of the occupied batch (at q)
-  void* inter;           // [TA*TJ][N][P2][P1] pair intermediates
+  void* inter;           // [TA*TJ][N][P2][LX] pair intermediates (kept f_x < P1 of each row)
   const void* vt;        // [P3][P2][P1] v(k-q+G)/N   (pass B)
   const void* dvt;       // [P3][P2][P1] dv/dmu/N^2   (pass B, mu-gradient)
   double2* acc;          // [TA][N^3] FP64 accumulators of the target batch
@@ -40,7 +42,10 @@ struct PairArgs {
   long long u_occ_stride;  // elements between consecutive occupied grids
   int TA, TJ;
   int h1, h2, h3, P1, P2, P3;
+  int LX;                // row pitch of the intermediates (>= P1; even in FP32, so a row
+                         // is a whole number of 16-byte units)
   double coef;           // -1 / N_q
+  int* err;              // device error flag (bit 2: a tensor-copy wait ran out)
 };
 
 struct GridArgs {        // sphere <-> grid
@@ -378,13 +383,16 @@ __device__ __forceinline__ void plane_inverse(const cplx<T>* tw, const cplx<T>* 
 // Forward z transform of a row of W pencils: load(z, c) real space,
 // out(kzb, c, value) for the kept |f_z| <= h3.  Warp-uniform n2 / k1, lanes
 // over c, so shared accesses are bank-conflict free and twiddles broadcast.
+// sZ holds N rows of pitch ld (0: W).  Step 1 reads and writes the same rows
+// of a column, so load may read sZ itself (an in-place transform).
 template <int N, int NT, typename T, typename Load, typename Out>
 __device__ __forceinline__ void pencil_forward(const cplx<T>* tw, cplx<T>* sZ, int W, int h3,
-                                              Load load, Out out) {
+                                              Load load, Out out, int ld = 0) {
   using C = cplx<T>;
   constexpr int A = Lay<N>::A, B = Lay<N>::B, NW = NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ncb = (W + 31) >> 5;
+  if (ld <= 0) ld = W;
 #pragma unroll 1
   for (int u = warp; u < B * ncb; u += NW) {
     const int n2 = u % B, c = lane + 32 * (u / B);
@@ -394,7 +402,7 @@ __device__ __forceinline__ void pencil_forward(const cplx<T>* tw, cplx<T>* sZ, i
       for (int n1 = 0; n1 < A; ++n1) r[n1] = load(B * n1 + n2, c);
       dft<A, false>(r);
 #pragma unroll
-      for (int k1 = 0; k1 < A; ++k1) sZ[(k1 * B + n2) * W + c] = tw_mul<false>(r[k1], tw[n2 * k1]);
+      for (int k1 = 0; k1 < A; ++k1) sZ[(k1 * B + n2) * ld + c] = tw_mul<false>(r[k1], tw[n2 * k1]);
     }
   }
   __syncthreads();
@@ -404,7 +412,7 @@ __device__ __forceinline__ void pencil_forward(const cplx<T>* tw, cplx<T>* sZ, i
     if (c < W) {
       C r[B];
 #pragma unroll
-      for (int n2 = 0; n2 < B; ++n2) r[n2] = sZ[(k1 * B + n2) * W + c];
+      for (int n2 = 0; n2 < B; ++n2) r[n2] = sZ[(k1 * B + n2) * ld + c];
       dft<B, false>(r);
 #pragma unroll
       for (int k2 = 0; k2 < B; ++k2) {
@@ -416,14 +424,15 @@ __device__ __forceinline__ void pencil_forward(const cplx<T>* tw, cplx<T>* sZ, i
 }
 
 // Inverse z transform of a row of W pencils from kept frequencies
-// load(kzb, c) to real space store(z, c, value).
+// load(kzb, c) to real space store(z, c, value); sZ rows of pitch ld (0: W).
 template <int N, int NT, typename T, typename Load, typename Store>
 __device__ __forceinline__ void pencil_inverse(const cplx<T>* tw, cplx<T>* sZ, int W, int h3,
-                                              Load load, Store store) {
+                                              Load load, Store store, int ld = 0) {
   using C = cplx<T>;
   constexpr int A = Lay<N>::A, B = Lay<N>::B, NW = NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ncb = (W + 31) >> 5;
+  if (ld <= 0) ld = W;
 #pragma unroll 1
   for (int u = warp; u < B * ncb; u += NW) {
     const int n2 = u % B, c = lane + 32 * (u / B);
@@ -436,7 +445,7 @@ __device__ __forceinline__ void pencil_inverse(const cplx<T>* tw, cplx<T>* sZ, i
       }
       dft<A, true>(r);
 #pragma unroll
-      for (int k1 = 0; k1 < A; ++k1) sZ[(k1 * B + n2) * W + c] = tw_mul<true>(r[k1], tw[n2 * k1]);
+      for (int k1 = 0; k1 < A; ++k1) sZ[(k1 * B + n2) * ld + c] = tw_mul<true>(r[k1], tw[n2 * k1]);
     }
   }
   __syncthreads();
@@ -446,7 +455,7 @@ __device__ __forceinline__ void pencil_inverse(const cplx<T>* tw, cplx<T>* sZ, i
     if (c < W) {
       C r[B];
 #pragma unroll
-      for (int n2 = 0; n2 < B; ++n2) r[n2] = sZ[(k1 * B + n2) * W + c];
+      for (int n2 = 0; n2 < B; ++n2) r[n2] = sZ[(k1 * B + n2) * ld + c];
       dft<B, true>(r);
 #pragma unroll
       for (int k2 = 0; k2 < B; ++k2) store(k1 + A * k2, c, r[k2]);
@@ -486,16 +495,16 @@ __global__ void __launch_bounds__(PassACfg<N, T>::NT, sizeof(T) == 4 ? 2 : 1) k_
   const int ta = blockIdx.x, z = blockIdx.y;
   constexpr long long plane = (long long)N * N;
   const C* ua = reinterpret_cast<const C*>(p.u_tgt) + ta * p.u_tgt_stride + z * plane;
-  const int P1 = p.P1;
+  const int LX = p.LX;
 #pragma unroll 1
   for (int tj = 0; tj < p.TJ; ++tj) {
     const C* uj = reinterpret_cast<const C*>(p.u_occ) + tj * p.u_occ_stride + z * plane;
     C* out = reinterpret_cast<C*>(p.inter) +
-             ((long long)(ta * p.TJ + tj) * N + z) * (long long)p.P2 * p.P1;
+             ((long long)(ta * p.TJ + tj) * N + z) * (long long)p.P2 * LX;
     plane_forward<N, T, false>(
         tw, s0, s1, p.h1, p.P1, p.h2,
         [&](int y, int x) { return cmulc(uj[y * N + x], ua[y * N + x]); },
-        [&](int kyb, int kxb, C v) { out[kyb * P1 + kxb] = v; });
+        [&](int kyb, int kxb, C v) { out[kyb * LX + kxb] = v; });
   }
 }
 
@@ -512,19 +521,172 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_pass_b(PairArgs 
   __syncthreads();
   const int kyb = blockIdx.x, pair = blockIdx.y;
   const int P1 = p.P1, P2 = p.P2;
-  const int zstride = P2 * P1;                 // a pair's planes stay within 32-bit offsets
-  C* row = reinterpret_cast<C*>(p.inter) + (long long)pair * N * zstride + kyb * P1;
+  const int zstride = P2 * p.LX;               // a pair's planes stay within 32-bit offsets
+  C* row = reinterpret_cast<C*>(p.inter) + (long long)pair * N * zstride + kyb * p.LX;
   const T* vt = reinterpret_cast<const T*>(p.vt) + kyb * P1;
   pencil_forward<N, NT, T>(
       tw, sZ, P1, p.h3, [&](int z, int c) { return row[z * zstride + c]; },
       [&](int kzb, int c, C v) {
-        const T s = vt[kzb * zstride + c];
+        const T s = vt[kzb * (P2 * P1) + c];
         sK[kzb * P1 + c] = s * v;
       });
   __syncthreads();
   pencil_inverse<N, NT, T>(
       tw, sZ, P1, p.h3, [&](int kzb, int c) { return sK[kzb * P1 + c]; },
       [&](int z, int c, C v) { row[z * zstride + c] = v; });
+}
+
+// --------------------------------------------- tensor-copy staged pass B --
+//
+// Bulk tensor copies (TMA) with mbarrier completion.  Every wait on an mbarrier
+// is bounded: after kMbarTries unsuccessful polls the caller sets an error flag
+// and leaves instead of spinning forever.
+
+constexpr unsigned kMbarTries = 1u << 22;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// makes the initialised barriers visible to the tensor-copy unit
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// true once the phase with the given parity has completed; false after
+// kMbarTries polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const unsigned a = smem_addr(bar);
+  for (unsigned i = 0; i < kMbarTries; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// orders this thread's earlier shared-memory accesses before later tensor copies
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 3-D tile load global -> shared, completion counted in bytes on bar
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Pass B, FP32, persistent and tensor-copy staged: item i = (pair i / P2, row
+// kyb = i % P2).  The row's N z-planes x LX values arrive by one 3-D tensor copy
+// (tm views the intermediates as [N * pairs][P2][2 LX] floats) into one of two
+// shared buffers, issued two items ahead, so the copy of the next row overlaps
+// this row's transforms.  The forward z step 1 runs in place in the buffer,
+// step 2 writes the kept f_z times v(k - q + G)/N to sK, the inverse step 1
+// writes back into the buffer and step 2 stores the row to global memory.
+// Tensor-copy destinations must be 128-byte aligned: the buffers start at the
+// first 128-byte boundary of the dynamic shared memory (the launch adds 128
+// bytes of slack) and each spans a multiple of 128 bytes.
+template <int N> __host__ __device__ constexpr int pass_b_tma_buf_elems(int LX) {
+  return (N * LX + 15) / 16 * 16;   // float2 elements, a multiple of 128 bytes
+}
+
+template <int N, int NT>
+__global__ void __launch_bounds__(NT, 2) k_pass_b_tma(const __grid_constant__ CUtensorMap tm, PairArgs p,
+                                                      int n_items) {
+  using C = float2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int ok;
+  const int LX = p.LX, P1 = p.P1, P2 = p.P2;
+  const unsigned pad = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
+  C* buf0 = reinterpret_cast<C*>(smem_raw + pad);
+  const int BUF = pass_b_tma_buf_elems<N>(LX);
+  C* sK = buf0 + 2 * BUF;
+  const C* tw = reinterpret_cast<const C*>(p.tw);
+  const unsigned bytes = (unsigned)(N * LX * sizeof(C));
+  const int G = gridDim.x;
+  const int zstride = P2 * LX;
+  // uniform across the block: never issue a copy to a misaligned buffer
+  if ((smem_addr(buf0) & 127u) != 0u || ((BUF * sizeof(C)) & 127u) != 0u) {
+    if (threadIdx.x == 0) atomicOr(p.err, 2);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+    for (int b = 0; b < 2; ++b) {
+      const int item = blockIdx.x + b * G;
+      if (item < n_items) {
+        mbar_arrive_expect_tx(&bar[b], bytes);
+        tma_load_3d(buf0 + b * BUF, &tm, 0, item % P2, (item / P2) * N, &bar[b]);
+      }
+    }
+    // one thread decides whether each row arrived, before the barrier that
+    // starts the row, so the whole block takes the same branch
+    ok = mbar_wait(&bar[0], 0) ? 1 : 0;
+  }
+  __syncthreads();
+  int it = 0;
+  for (int item = blockIdx.x; item < n_items; item += G, ++it) {
+    const int b = it & 1;
+    C* X = buf0 + b * BUF;
+    if (!ok) {
+      // the copy never completed: flag it, give the other buffer's copy (if
+      // any) its bounded wait, and leave
+      if (threadIdx.x == 0) {
+        atomicOr(p.err, 2);
+        if (item + G < n_items) mbar_wait(&bar[b ^ 1], ((it + 1) >> 1) & 1);
+      }
+      return;
+    }
+    // completes at once: makes the copied bytes visible to every thread
+    mbar_wait(&bar[b], (it >> 1) & 1);
+    const int kyb = item % P2, pair = item / P2;
+    const float* vt = reinterpret_cast<const float*>(p.vt) + kyb * P1;
+    pencil_forward<N, NT, float>(
+        tw, X, P1, p.h3, [&](int z, int c) { return X[z * LX + c]; },
+        [&](int kzb, int c, C v) { sK[kzb * P1 + c] = vt[kzb * (P2 * P1) + c] * v; }, LX);
+    __syncthreads();
+    C* row = reinterpret_cast<C*>(p.inter) + (long long)pair * N * zstride + kyb * LX;
+    pencil_inverse<N, NT, float>(
+        tw, X, P1, p.h3, [&](int kzb, int c) { return sK[kzb * P1 + c]; },
+        [&](int z, int c, C v) { row[z * zstride + c] = v; }, LX);
+    // the next row's copy was issued two rows ago: wait for it before the
+    // barrier (bounded), so the barrier both frees X and publishes the decision
+    if (threadIdx.x == 0 && item + G < n_items) ok = mbar_wait(&bar[b ^ 1], ((it + 1) >> 1) & 1) ? 1 : 0;
+    __syncthreads();   // every read of X and sK is done
+    const int next = item + 2 * G;
+    if (threadIdx.x == 0 && next < n_items) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bar[b], bytes);
+      tma_load_3d(X, &tm, 0, next % P2, (next / P2) * N, &bar[b]);
+    }
+  }
+}
+
+// dynamic shared memory of k_pass_b_tma: 128 bytes of alignment slack, two
+// row buffers, the kept-f_z block
+template <int N> constexpr size_t smem_pass_b_tma(int LX, int P1, int P3) {
+  return 128 + sizeof(float2) * ((size_t)2 * pass_b_tma_buf_elems<N>(LX) + (size_t)P3 * P1);
 }
 
 // Pass B for dE/dmu: forward z only, partial[pair][kyb] = sum dv/dmu/N^2 |rho|^2.
@@ -539,8 +701,8 @@ __global__ void __launch_bounds__(NT) k_pass_b_dmu(PairArgs p) {
   __syncthreads();
   const int kyb = blockIdx.x, pair = blockIdx.y;
   const int P1 = p.P1, P2 = p.P2;
-  const long long zstride = (long long)P2 * P1;
-  const C* row = reinterpret_cast<const C*>(p.inter) + (long long)pair * N * zstride + (long long)kyb * P1;
+  const long long zstride = (long long)P2 * p.LX;
+  const C* row = reinterpret_cast<const C*>(p.inter) + (long long)pair * N * zstride + (long long)kyb * p.LX;
   const T* dvt = reinterpret_cast<const T*>(p.dvt);
   double s = 0.0;
   pencil_forward<N, NT, T>(
@@ -580,7 +742,7 @@ __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_c(PairArgs p) {
   __syncthreads();
   const int ta = blockIdx.x, z = blockIdx.y;
   constexpr long long plane = (long long)N * N;
-  const int P1 = p.P1;
+  const int LX = p.LX;
   C acc[G::X2_IT][B];
 #pragma unroll
   for (int i = 0; i < G::X2_IT; ++i)
@@ -589,7 +751,7 @@ __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_c(PairArgs p) {
 #pragma unroll 1
   for (int tj = 0; tj < p.TJ; ++tj) {
     const C* in = reinterpret_cast<const C*>(p.inter) +
-                  ((long long)(ta * p.TJ + tj) * N + z) * (long long)p.P2 * p.P1;
+                  ((long long)(ta * p.TJ + tj) * N + z) * (long long)p.P2 * LX;
     const C* uj = reinterpret_cast<const C*>(p.u_occ) + tj * p.u_occ_stride + z * plane;
     T cf, cf2;
     if (PACKED) {
@@ -600,10 +762,10 @@ __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_c(PairArgs p) {
       cf = (T)(p.coef * p.w_occ[tj]);
       cf2 = (T)0;
     }
-    const long long pbytes = (long long)p.P2 * p.P1 * (long long)sizeof(C);
-    const C* next = tj + 1 < p.TJ ? in + (long long)N * p.P2 * p.P1 : nullptr;
+    const long long pbytes = (long long)p.P2 * LX * (long long)sizeof(C);
+    const C* next = tj + 1 < p.TJ ? in + (long long)N * p.P2 * LX : nullptr;
     plane_inverse<N, T, false>(
-        tw, tw2, s0, s1, p.h1, p.P1, p.h2, [&](int kyb, int kxb) { return in[kyb * P1 + kxb]; },
+        tw, tw2, s0, s1, p.h1, p.P1, p.h2, [&](int kyb, int kxb) { return in[kyb * LX + kxb]; },
         [&](int i, int k2, int y, int x, C v) {
           const C u = uj[y * N + x];
           if (PACKED) {
@@ -664,8 +826,8 @@ __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_ct(PairArgs p) {
   __syncthreads();
   const int tj = blockIdx.x, z = blockIdx.y;
   constexpr long long plane = (long long)N * N;
-  const int P1 = p.P1;
-  const long long pstride = (long long)p.P2 * p.P1;
+  const int LX = p.LX;
+  const long long pstride = (long long)p.P2 * LX;
   C acc[G::X2_IT][B];
 #pragma unroll
   for (int i = 0; i < G::X2_IT; ++i)
@@ -678,7 +840,7 @@ __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_ct(PairArgs p) {
     const C* next = ta + 1 < p.TA ? in + (long long)p.TJ * N * pstride : nullptr;
     const T wa = p.w_tgt ? (T)p.w_tgt[ta] : (T)1;
     plane_inverse<N, T, false>(
-        tw, tw2, s0, s1, p.h1, p.P1, p.h2, [&](int kyb, int kxb) { return in[kyb * P1 + kxb]; },
+        tw, tw2, s0, s1, p.h1, p.P1, p.h2, [&](int kyb, int kxb) { return in[kyb * LX + kxb]; },
         [&](int i, int k2, int y, int x, C v) {
           const C t = cmulc(v, fa[y * N + x]);   // conj(W) * f_a
           acc[i][k2].x += wa * t.x;
@@ -806,9 +968,9 @@ __global__ void __launch_bounds__(NT) k_pass_b_strain(PairArgs p) {
   __syncthreads();
   const int kyb = blockIdx.x, pair = blockIdx.y;
   const int P1 = p.P1, P2 = p.P2;
-  const long long zstride = (long long)P2 * P1;
-  const long long nbox = zstride * p.P3;
-  const C* row = reinterpret_cast<const C*>(p.inter) + (long long)pair * N * zstride + (long long)kyb * P1;
+  const long long zstride = (long long)P2 * p.LX;
+  const long long nbox = (long long)P2 * P1 * p.P3;
+  const C* row = reinterpret_cast<const C*>(p.inter) + (long long)pair * N * zstride + (long long)kyb * p.LX;
   const T* tab = reinterpret_cast<const T*>(p.dvt);
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   pencil_forward<N, NT, T>(

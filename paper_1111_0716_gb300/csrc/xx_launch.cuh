@@ -24,6 +24,10 @@ struct KernelSet {
 struct KernelTable {
   int n;
   KernelSet f32, f64;
+  // FP32 pass B staged by tensor copies (persistent grid of `grid` CTAs), and
+  // its resident CTAs per SM for a given intermediate shape
+  void (*pass_b_tma)(const PairArgs&, const CUtensorMap&, int grid, cudaStream_t);
+  int (*pass_b_tma_per_sm)(int LX, int P1, int P3);
   void (*g2s_xy)(const GridArgs&, cudaStream_t);
   void (*g2s_z)(const GridArgs&, cudaStream_t);
 };
@@ -45,6 +49,21 @@ template <int N, typename T> void launch_pass_b(const PairArgs& p, cudaStream_t 
   const size_t sm = smem_pencil<N, T>(p.P1, p.P3);
   allow_smem(k_pass_b<N, kThreads, T>, sm);
   k_pass_b<N, kThreads, T><<<dim3(p.P2, p.TA * p.TJ), kThreads, sm, s>>>(p);
+}
+template <int N> void launch_pass_b_tma(const PairArgs& p, const CUtensorMap& tm, int grid, cudaStream_t s) {
+  const size_t sm = smem_pass_b_tma<N>(p.LX, p.P1, p.P3);
+  allow_smem(k_pass_b_tma<N, kThreads>, sm);
+  k_pass_b_tma<N, kThreads><<<grid, kThreads, sm, s>>>(tm, p, p.P2 * p.TA * p.TJ);
+}
+template <int N> int pass_b_tma_per_sm(int LX, int P1, int P3) {
+  const size_t sm = smem_pass_b_tma<N>(LX, P1, P3);
+  allow_smem(k_pass_b_tma<N, kThreads>, sm);
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pass_b_tma<N, kThreads>, kThreads, sm) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 template <int N, typename T> void launch_pass_b_dmu(const PairArgs& p, cudaStream_t s) {
   const size_t sm = smem_pencil<N, T>(p.P1, 0);
@@ -102,6 +121,8 @@ template <int N> const KernelTable* make_table() {
        launch_pass_b_strain<N, double>, launch_pass_c<N, double, false>, launch_pass_c<N, double, true>,
        launch_pass_ct<N, double>, launch_s2g_z<N, double>,
        launch_s2g_xy<N, double>},
+      launch_pass_b_tma<N>,
+      pass_b_tma_per_sm<N>,
       launch_g2s_xy<N>,
       launch_g2s_z<N>};
   return &t;

@@ -36,10 +36,12 @@ XX_NOALLOC_MAX_ROWS = 16384
 EXPORTS = ("xx_create", "xx_destroy", "xx_apply", "xx_apply_range", "xx_energy",
            "xx_energy_range", "xx_energy_from_vx", "xx_energy_from_vx_range",
            "xx_apply_backward", "xx_sync", "xx_set_batch", "xx_profile_enable",
-           "xx_profile_read", "xx_plan_info", "xx_status_string", "xx_energy_from_vx_noalloc",
-           "xx_run_many", "xx_apply_vjp", "xx_set_option", "xx_strain_derivative")
+           "xx_profile_read", "xx_plan_info", "xx_status_string", "xx_exact_grid",
+           "xx_energy_from_vx_noalloc", "xx_run_many", "xx_apply_vjp", "xx_set_option",
+           "xx_strain_derivative")
 XX_OPT_PAIR_SYMMETRY = 0
 XX_OPT_REAL_GAMMA = 1
+XX_OPT_TMA_PASS_B = 2
 
 PROF_CLASSES = ("pass_a", "pass_b", "pass_c", "sphere_to_grid", "grid_to_sphere",
                 "kernel_table", "reduce", "pass_b_dmu")
@@ -101,6 +103,7 @@ def load(path: Optional[str] = None):
     lib.xx_set_option.argtypes = [P, I, ctypes.c_longlong]
     lib.xx_strain_derivative.argtypes = [P, P, P, I, P, P, P]
     lib.xx_status_string.argtypes = [I]
+    lib.xx_exact_grid.argtypes = [P, P]
     lib.xx_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name not in ("xx_status_string",):
@@ -270,6 +273,14 @@ def xx_profile_read(plan, reset: bool = True) -> dict:
     return {c: (float(ms[i]), int(cnt[i])) for i, c in enumerate(PROF_CLASSES)}
 
 
+def xx_exact_grid(n_max) -> int:
+    """Smallest supported cubic FFT length N >= 4 n_max + 1 (the operator is exact there)."""
+    nm = np.ascontiguousarray(np.asarray(n_max, dtype=np.int32).reshape(3))
+    out = np.zeros(1, dtype=np.int32)
+    _check(load().xx_exact_grid(_np_ptr(nm), _np_ptr(out)), "xx_exact_grid")
+    return int(out[0])
+
+
 def xx_plan_info(plan) -> dict:
     info = xx_info()
     _check(load().xx_plan_info(plan, ctypes.byref(info)), "xx_plan_info")
@@ -320,6 +331,10 @@ class Plan:
 
     def set_pair_symmetry(self, enable: bool):
         xx_set_option(self.handle, XX_OPT_PAIR_SYMMETRY, 1 if enable else 0)
+
+    def set_tma_pass_b(self, mode: int):
+        """0: one-row-per-block pass B; 1: automatic (default); 2: tensor-copy kernel."""
+        xx_set_option(self.handle, XX_OPT_TMA_PASS_B, int(mode))
 
     def set_real_gamma(self, enable: bool):
         """Declare the orbitals of later calls real in real space (Gamma-only plans)."""

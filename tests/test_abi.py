@@ -109,3 +109,19 @@ def test_no_device_is_reported_without_a_gpu(lib):
         pytest.skip("a GPU is present")
     wl = synth.tiny_cubic()
     assert _status(lambda: _create(lib, wl)) == -8
+
+
+def test_exact_grid_is_the_smallest_admissible_supported_length(lib):
+    """xx_exact_grid: the smallest supported N with N >= 4 n_max + 1 on every axis."""
+    supported = (24, 32, 40, 48, 60, 64, 72, 80, 96)
+    for nm in [(0, 0, 0), (4, 4, 4), (5, 4, 4), (7, 7, 7), (7, 9, 8), (14, 14, 14), (14, 12, 13),
+               (15, 15, 15), (23, 1, 1)]:
+        need = 4 * max(nm) + 1
+        assert lib.xx_exact_grid(nm) == min(n for n in supported if n >= need)
+    # the workloads' grids are admissible, and their smallest exact grids are smaller
+    for wl, n in [(synth.tiny_cubic(), 24), (synth.beta_boron(), 60)]:
+        nm = wl.n_max()
+        assert lib.xx_exact_grid(nm) == n
+        assert wl.grid[0] >= 4 * nm.max() + 1
+    assert _status(lambda: lib.xx_exact_grid((24, 0, 0))) == -2
+    assert _status(lambda: lib.xx_exact_grid((-1, 0, 0))) == -1

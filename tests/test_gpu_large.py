@@ -42,6 +42,16 @@ def test_alpha_boron_48_mp444(gpu, oracle_mod):
     assert gu.rel_max(got, ref) <= gu.FP32_TOL
     v64 = fp64_target_slice(xx, wl, *sel[1])
     assert gu.rel_max(v64, ref[1]) <= gu.FP64_TOL
+    # the smallest exact grid (32^3 for n_max = 7) gives the same operator as 48^3,
+    # in both precisions
+    n = xx.xx_exact_grid(wl.n_max())
+    assert n == 32
+    small = wl.replace(grid=(n,) * 3)
+    vx32, (e32, _), _ = gu.run(small, 0)
+    assert gu.rel_max(np.stack([vx32[k, a] for k, a in sel]), ref) <= gu.FP32_TOL
+    assert abs(e32 - e) <= gu.FP32_TOL * abs(e)
+    w64 = fp64_target_slice(xx, small, *sel[1])
+    assert gu.rel_max(w64, ref[1]) <= gu.FP64_TOL
 
 
 @pytest.mark.slow
@@ -60,3 +70,10 @@ def test_beta_boron_96_gamma222(gpu, oracle_mod):
     assert abs(d_gpu - d_ref) <= gu.FP32_TOL * abs(d_ref)
     v64 = fp64_target_slice(xx, wl, k, a)
     assert gu.rel_max(v64, ref) <= gu.FP64_TOL
+    # the smallest exact grid (60^3 for n_max = 14) gives the same operator as 96^3
+    n = xx.xx_exact_grid(wl.n_max())
+    assert n == 60
+    vx60, (e60, _), _ = gu.run(wl.replace(grid=(n,) * 3), 0)
+    assert gu.rel_max(vx60[k, a], ref) <= gu.FP32_TOL
+    assert abs(e60 - e) <= gu.FP32_TOL * abs(e)
+    assert gu.rel_max(vx60, vx) <= gu.FP32_TOL

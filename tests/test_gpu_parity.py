@@ -258,3 +258,28 @@ def test_pair_symmetry_transform_count(gpu):
         plan.close()
         assert n == expected_transforms(wl.nk, wl.n_occ, wl.n_tgt, 3, 3, on)
     assert expected_transforms(wl.nk, wl.n_occ, wl.n_tgt, 3, 3, True) < logical
+
+
+@pytest.mark.parametrize("make", [synth.tiny_cubic, rhombo24] +
+                         [lambda i=i: synth.sweep_cell(i) for i in range(len(synth.SWEEP_GRIDS))])
+def test_tma_pass_b_matches_row_kernel(gpu, make):
+    """FP32 pass B staged by bulk tensor copies (forced on) against the one-row-per-block
+    kernel, on every grid length the sweep uses; ragged batches."""
+    torch, xx = gpu
+    wl = make()
+    out = []
+    for tma in (2, 0):
+        plan = xx.Plan.from_workload(wl, precision=0)
+        plan.set_batch(5, 3)
+        plan.set_tma_pass_b(tma)
+        c = gu.dev(wl.c_tgt)
+        ex, vx = plan.energy(c, gu.dev(wl.w_occ), c, gu.dev(wl.w_tgt), shared=True)
+        plan.sync(timeout_s=600.0)
+        out.append((vx.cpu().numpy(), float(ex[0].item())))
+        plan.close()
+    assert gu.rel_max(out[0][0], out[1][0]) <= 1e-6
+    assert abs(out[0][1] - out[1][1]) <= 1e-6 * abs(out[1][1])
+    plan = xx.Plan.from_workload(wl, precision=0)
+    with pytest.raises(xx.XXError):
+        plan.set_tma_pass_b(3)
+    plan.close()
