@@ -244,8 +244,10 @@ int xx_run_many(int n_jobs, const xx_job *jobs, void *stream);
  *       (the codensity conj(u_qj) u_ka and the multiplication by u_qj):
  *       dL/dc_qj* = P_q[ -(w_qj/N_k) sum_{k,a} (ubar_ka conj(W_aj) + u_ka conj(Wbar_aj)) ]
  *       with ubar the grids of ybar, W_aj the pair potential of (u_ka, u_qj) and
- *       Wbar_aj that of (ubar_ka, u_qj).  Costs about two forward applications;
- *       pair potentials are recomputed, never stored beyond one batch.
+ *       Wbar_aj that of (ubar_ka, u_qj).  With both outputs requested the two
+ *       cost two transforms per band pair (XX_OPT_FUSED_VJP), else one (target
+ *       part) and two (occupied part); pair potentials are recomputed, never
+ *       stored beyond one batch.
  * When the same orbitals are both occupied and targets, the total gradient
  * is the sum of the two outputs.  Occupations are treated as constants.
  */
@@ -298,6 +300,31 @@ int xx_sync(xx_plan plan, void *stream, double timeout_s);
                                    kernel; 2 always the tensor-copy kernel; 0 never.  Both
                                    run the same arithmetic in the same order.  Other values
                                    give XX_ERR_INVALID_ARGUMENT. */
+
+#define XX_OPT_STAGE_PASS_A 3   /* FP32 pass A: 2 runs one CTA per SM with the occupied
+                                   orbital's plane staged in shared memory by one bulk copy
+                                   per band, issued while the previous band's plane is being
+                                   transformed; 0 runs two CTAs per SM reading both planes
+                                   with global loads; 1 (default) stages for grid lengths up
+                                   to 64.  Same arithmetic in the same order.  Other values
+                                   give XX_ERR_INVALID_ARGUMENT. */
+
+#define XX_OPT_TEST_WAIT_EXPIRY 4 /* tests of the failure path only: value != 0 announces the
+                                   first tensor copy of every pass-B CTA as 16 bytes longer
+                                   than it is, so the bounded wait on it (2 s) runs out; the
+                                   CTA then sets the device flag and returns.  Results of
+                                   such a call are invalid; xx_sync reports
+                                   XX_ERR_DEVICE_FLAG and the context stays usable.  Takes
+                                   effect only where the tensor-copy pass B runs.  Default 0. */
+
+#define XX_OPT_FUSED_VJP 5      /* value != 0 (default): xx_apply_vjp asked for both gradients
+                                   transforms each band pair twice instead of three times: the
+                                   pair potential of (ubar_ka, u_qj) feeds both V_x ybar and the
+                                   u_ka conj(Wbar) term of the occupied gradient.  Needs FP64
+                                   accumulators of every occupied band of every k-point
+                                   (nk * n_occ * N^3 * 16 bytes, at most 64 GiB); otherwise,
+                                   or with 0, the two gradients are computed one after the
+                                   other.  Results differ only by rounding order. */
 
 /* Set a plan option; XX_ERR_INVALID_ARGUMENT for an unknown option. */
 int xx_set_option(xx_plan plan, int option, long long value);

@@ -280,6 +280,9 @@ struct xx_plan_s {
   int ta_user = 0, tj_user = 0;
   bool pair_symmetry = true;
   int tma_pass_b = 1;          // XX_OPT_TMA_PASS_B: 0 off, 1 when pruning keeps <= 3/4 of a row, 2 always
+  int stage_pass_a = 1;        // XX_OPT_STAGE_PASS_A: 0 off, 1 for N <= 64, 2 always
+  bool test_wait_expiry = false;   // XX_OPT_TEST_WAIT_EXPIRY
+  bool fused_vjp = true;           // XX_OPT_FUSED_VJP
   int sm_count = 0;
   int tma_per_sm = -1;         // resident tensor-copy pass B CTAs per SM (-1: not queried)
   bool real_gamma = false;     // XX_OPT_REAL_GAMMA
@@ -547,6 +550,11 @@ PairArgs pair_args(xx_plan p, int TA, int TJ) {
   a.LX = LX(p);
   a.coef = -1.0 / (double)p->nk;
   a.err = p->d_err;
+  a.test_wait_expiry = p->test_wait_expiry ? 1 : 0;
+  // measured on GB300 (beta cell, 64 targets x 160 occupied x 8 q, pass A): staged
+  // 5.6 % faster at N = 60, 13 % slower at N = 96 (one CTA of 768 threads per SM
+  // against two of 384)
+  a.stage_a = p->prec == XX_FP32_MIXED && (p->stage_pass_a == 2 || (p->stage_pass_a == 1 && p->N <= 64)) ? 1 : 0;
   return a;
 }
 
@@ -1149,6 +1157,80 @@ int run_vjp_occ(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, i
   return XX_OK;
 }
 
+// Both parts of the vector-Jacobian product from two transforms per band pair:
+// Wbar_aj = K(conj(u_qj) ubar_ka) feeds dL/dc_tgt* = V_x ybar (pass C into the
+// accumulators of the targets of k) and the u_ka conj(Wbar_aj) term of
+// dL/dc_qj* (role-swapped pass C); W_aj = K(conj(u_qj) u_ka) feeds the
+// ubar_ka conj(W_aj) term.  The occupied accumulators of every q are held at
+// once (nk * n_occ * N^3 * 16 bytes).  Returns XX_ERR_OUT_OF_MEMORY (nothing
+// launched beyond the grids) when they do not fit, so the caller can run the
+// two parts separately.
+int run_vjp_fused(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, int n_occ,
+                  const void* c_tgt, int n_tgt, const void* ybar, void* grad_tgt, void* grad_occ,
+                  cudaStream_t s) {
+  const long long nn = n3(p);
+  const size_t occ_bytes = (size_t)p->nk * n_occ * nn * 16;
+  if (occ_bytes > kCrossAccCap) return XX_ERR_OUT_OF_MEMORY;
+  const bool shared = (c_occ == c_tgt && ld_occ == n_tgt);
+  int st = build_grids(p, 0, p->nk, c_occ, ld_occ, n_occ, c_tgt, n_tgt, shared, s);
+  if (st) return st;
+  const size_t eb = elem_bytes(p);
+  if ((st = ensure(p, p->u_bar, (size_t)p->nk * n_tgt * nn * eb))) return st;
+  for (int k = 0; k < p->nk; ++k) {
+    st = sphere_to_grid(p, k, (const double2*)ybar + (long long)k * n_tgt * p->npw_max, n_tgt,
+                        (char*)p->u_bar.p + (size_t)k * n_tgt * nn * eb, s);
+    if (st) return st;
+  }
+  int TA, TJ;
+  batch_shape(p, n_tgt, n_occ, &TA, &TJ);
+  if ((st = ensure(p, p->inter, (size_t)TA * TJ * inter_pair_bytes(p)))) return st;
+  if ((st = ensure(p, p->acc2, occ_bytes))) return st;
+  if ((st = ensure(p, p->acc, (size_t)n_tgt * nn * 16))) return st;
+  cudaMemsetAsync(p->acc2.p, 0, occ_bytes, s);
+  for (int k = 0; k < p->nk; ++k) {
+    cudaMemsetAsync(p->acc.p, 0, (size_t)n_tgt * nn * 16, s);
+    for (int q = 0; q < p->nk; ++q) {
+      if ((st = kernel_table_for(p, k, q, false, s))) return st;
+      double2* acc_q = (double2*)p->acc2.p + (long long)q * n_occ * nn;
+      for (int a0 = 0; a0 < n_tgt; a0 += TA) {
+        const int ta = (n_tgt - a0) < TA ? (n_tgt - a0) : TA;
+        for (int j0 = 0; j0 < n_occ; j0 += TJ) {
+          const int tj = (n_occ - j0) < TJ ? (n_occ - j0) : TJ;
+          const char* ut = grid_ptr(p, true, k, a0, n_occ, n_tgt);
+          const char* ub = (const char*)p->u_bar.p + ((size_t)k * n_tgt + a0) * nn * eb;
+          PairArgs a = pair_args(p, ta, tj);
+          a.u_occ = grid_ptr(p, shared, q, j0, n_occ, n_tgt);
+          a.w_occ = w_occ + (long long)q * n_occ + j0;
+          // Wbar: V_x ybar for the targets of k, and u_a conj(Wbar) for j
+          a.u_tgt = ub;
+          run_pass_a(p, a, s);
+          run_pass_b(p, a, s);
+          a.acc = (double2*)p->acc.p + (long long)a0 * nn;
+          run_pass_c(p, a, s);
+          a.u_tgt = ut;
+          a.acc = acc_q + (long long)j0 * nn;
+          run_pass_ct(p, a, s);
+          // W: ubar_a conj(W) for j
+          run_pass_a(p, a, s);
+          run_pass_b(p, a, s);
+          a.u_tgt = ub;
+          run_pass_ct(p, a, s);
+          if ((st = launched(p, 7))) return st;
+        }
+      }
+    }
+    st = grid_to_sphere(p, k, (const double2*)p->acc.p, n_tgt,
+                        (double2*)grad_tgt + (long long)k * n_tgt * p->npw_max, s);
+    if (st) return st;
+  }
+  for (int q = 0; q < p->nk; ++q) {
+    st = grid_to_sphere(p, q, (const double2*)p->acc2.p + (long long)q * n_occ * nn, n_occ,
+                        (double2*)grad_occ + (long long)q * n_occ * p->npw_max, s);
+    if (st) return st;
+  }
+  return XX_OK;
+}
+
 bool supported_grid(const int* g) { return g[0] == g[1] && g[1] == g[2] && supported_n(g[0]); }
 
 }  // namespace
@@ -1487,6 +1569,13 @@ int xx_apply_vjp(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, 
   for (const void* o : outs)
     if (o && (o == c_occ || o == c_tgt || o == ybar)) return XX_ERR_INVALID_ARGUMENT;
   int st;
+  if (grad_tgt_out && n_tgt > 0 && grad_occ_out && n_occ > 0 && p->fused_vjp) {
+    if (bad_ptr(c_occ) || bad_ptr(w_occ) || bad_ptr(c_tgt)) return XX_ERR_INVALID_ARGUMENT;
+    st = run_vjp_fused(p, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, ybar, grad_tgt_out,
+                       grad_occ_out, s);
+    if (st != XX_ERR_OUT_OF_MEMORY) return st;
+    // the occupied accumulators of every q do not fit: the two parts one after the other
+  }
   if (grad_tgt_out && n_tgt > 0) {
     // V_x is Hermitian: dL/dc_tgt* = V_x ybar (a complex cotangent: general path)
     if ((st = apply_range(p, 0, p->nk, c_occ, ld_occ, w_occ, n_occ, ybar, n_tgt, grad_tgt_out,
@@ -1551,6 +1640,16 @@ int xx_set_option(xx_plan p, int option, long long value) {
     case XX_OPT_REAL_GAMMA:
       if (value != 0 && !p->gamma_closed) return XX_ERR_INVALID_ARGUMENT;
       p->real_gamma = value != 0;
+      return XX_OK;
+    case XX_OPT_FUSED_VJP:
+      p->fused_vjp = value != 0;
+      return XX_OK;
+    case XX_OPT_TEST_WAIT_EXPIRY:
+      p->test_wait_expiry = value != 0;
+      return XX_OK;
+    case XX_OPT_STAGE_PASS_A:
+      if (value < 0 || value > 2) return XX_ERR_INVALID_ARGUMENT;
+      p->stage_pass_a = (int)value;
       return XX_OK;
     case XX_OPT_TMA_PASS_B:
       if (value < 0 || value > 2) return XX_ERR_INVALID_ARGUMENT;

@@ -46,6 +46,9 @@ struct PairArgs {
                          // is a whole number of 16-byte units)
   double coef;           // -1 / N_q
   int* err;              // device error flag (bit 2: a tensor-copy wait ran out)
+  int stage_a;           // FP32 pass A: occupied planes by bulk copies into shared memory
+  int test_wait_expiry;  // tests only: announce the first pass-B copy of each CTA 16
+                         // bytes longer than it is, so its bounded wait runs out
 };
 
 struct GridArgs {        // sphere <-> grid
@@ -105,11 +108,14 @@ constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
 // iteration covers whole rows) and register holds across barriers.  The
 // default is two buffers for FP32 (pass C keeps its accumulator in registers)
 // and one for FP64 (two FP64 buffers exceed shared memory).
-template <int N, typename T, bool DB_ = (sizeof(T) == 4)> struct PlaneCfg {
+// NT_ > 0 overrides the thread count (the one-buffer variant then needs it to be a
+// multiple of 32, of B and, when A != 8, of A).
+template <int N, typename T, bool DB_ = (sizeof(T) == 4), int NT_ = 0> struct PlaneCfg {
   static constexpr int A = Lay<N>::A, B = Lay<N>::B, S = Lay<N>::S, LD = Lay<N>::LD;
   static constexpr bool DB = DB_;
-  static constexpr int NT = DB ? round_up(N * A, 32)
-                               : round_up(N * A / 2, lcm_c(lcm_c(32, B), A == 8 ? 1 : A));
+  static constexpr int NT = NT_ > 0 ? NT_
+                            : DB ? round_up(N * A, 32)
+                                 : round_up(N * A / 2, lcm_c(lcm_c(32, B), A == 8 ? 1 : A));
   static constexpr int NW = NT / 32;
   static constexpr bool REG_TW = (NT % B) == 0;                    // thread's x-step n2 fixed
   static constexpr int X1_IT = (N * B + NT - 1) / NT;
@@ -122,6 +128,10 @@ template <int N, typename T, bool DB_ = (sizeof(T) == 4)> struct PlaneCfg {
   static_assert(NT <= 1024, "too many threads");
   // twiddles (N) + [k1][n2] twiddle table (N) + plane buffer(s)
   static constexpr size_t smem() { return sizeof(cplx<T>) * ((size_t)2 * N + (size_t)BUF * (DB ? 2 : 1)); }
+};
+
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
 };
 
 // Cooperative L1 prefetch of [p, p + bytes): one 128-byte line per thread.
@@ -146,11 +156,16 @@ template <int A> __device__ __forceinline__ void x2_item(int it, int& k1, int& r
 // Forward x then y transform of one real-space plane; outputs only the kept
 // frequencies |f_x| <= h1, |f_y| <= h2 through store(kyb, kxb, value).
 // s0 (and s1 when double-buffered) are the plane buffers.
-template <int N, typename T, bool DB, typename Load, typename Store>
+// after_x1() runs on every thread right after the barrier that ends the first x
+// step (the last use of load); before_end() right before the final barrier.
+// NTO overrides the thread count of PlaneCfg (0: its default).
+template <int N, typename T, bool DB, int NTO = 0, typename Load, typename Store, typename AfterX1 = NoHook,
+          typename BeforeEnd = NoHook>
 __device__ __forceinline__ void plane_forward(const cplx<T>* tw, cplx<T>* s0, cplx<T>* s1, int h1,
-                                              int P1, int h2, Load load, Store store) {
+                                              int P1, int h2, Load load, Store store,
+                                              AfterX1 after_x1 = AfterX1(), BeforeEnd before_end = BeforeEnd()) {
   using C = cplx<T>;
-  using G = PlaneCfg<N, T, DB>;
+  using G = PlaneCfg<N, T, DB, NTO>;
   constexpr int A = G::A, B = G::B, S = G::S, LD = G::LD, NT = G::NT, NW = G::NW;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   C* sy = G::DB ? s1 : s0;   // buffer of the natural-order plane
@@ -175,6 +190,7 @@ __device__ __forceinline__ void plane_forward(const cplx<T>* tw, cplx<T>* s0, cp
     }
   }
   __syncthreads();
+  after_x1();
   // x, step 2: length-B DFTs, output at natural f_x positions
   if constexpr (G::DB) {
 #pragma unroll
@@ -246,6 +262,7 @@ __device__ __forceinline__ void plane_forward(const cplx<T>* tw, cplx<T>* s0, cp
       }
     }
   }
+  before_end();
   __syncthreads();
 }
 
@@ -539,10 +556,16 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_pass_b(PairArgs 
 // --------------------------------------------- tensor-copy staged pass B --
 //
 // Bulk tensor copies (TMA) with mbarrier completion.  Every wait on an mbarrier
-// is bounded: after kMbarTries unsuccessful polls the caller sets an error flag
-// and leaves instead of spinning forever.
+// is bounded: after kMbarLimitNs of unsuccessful polls (global timer) the caller
+// sets an error flag and leaves instead of spinning forever.
 
-constexpr unsigned kMbarTries = 1u << 22;
+constexpr unsigned long long kMbarLimitNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -562,11 +585,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned by
                : "memory");
 }
 
-// true once the phase with the given parity has completed; false after
-// kMbarTries polls
+// true once the phase with the given parity has completed; false when it has
+// not completed kMbarLimitNs after the first unsuccessful poll
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   const unsigned a = smem_addr(bar);
-  for (unsigned i = 0; i < kMbarTries; ++i) {
+  unsigned long long t0 = 0;
+  for (;;) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -575,8 +599,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
+    const unsigned long long now = global_ns();
+    if (t0 == 0)
+      t0 = now;
+    else if (now - t0 > kMbarLimitNs)
+      return false;
   }
-  return false;
 }
 
 // orders this thread's earlier shared-memory accesses before later tensor copies
@@ -593,6 +621,57 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
       "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
       : "memory");
 }
+
+// contiguous global -> shared bulk copy (16-byte aligned ends), completion on bar
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Shared staging of the pair-intermediate planes read by pass C (one plane of
+// P2 x LX values per loop step, contiguous in global memory): the plane of step
+// s + 1 is copied in by one bulk copy issued as soon as step s has read its
+// plane (after the first y step), and waited for before step s ends.  All waits
+// are bounded; a wait that runs out makes every thread leave (ok == 0).
+struct PlaneStage {
+  uint64_t* bar;
+  int* ok;
+  void* buf;
+  unsigned bytes;
+  __device__ __forceinline__ void start(const void* first) {
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      mbar_init_fence();
+      mbar_arrive_expect_tx(bar, bytes);
+      bulk_load(buf, first, bytes, bar);
+      *ok = mbar_wait(bar, 0) ? 1 : 0;
+    }
+    __syncthreads();
+  }
+  // start of step s: false (on every thread) when the copy never completed
+  __device__ __forceinline__ bool ready(int s) {
+    if (!*ok) {
+      if (threadIdx.x == 0) atomicOr(err_flag, 2);
+      return false;
+    }
+    mbar_wait(bar, (unsigned)(s & 1));   // completes at once; publishes the bytes
+    return true;
+  }
+  __device__ __forceinline__ void issue(const void* next) {
+    if (threadIdx.x == 0 && next) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(bar, bytes);
+      bulk_load(buf, next, bytes, bar);
+    }
+  }
+  __device__ __forceinline__ void wait_next(int s, bool has_next) {
+    if (threadIdx.x == 0 && has_next) *ok = mbar_wait(bar, (unsigned)((s + 1) & 1)) ? 1 : 0;
+  }
+  int* err_flag;
+};
 
 // Pass B, FP32, persistent and tensor-copy staged: item i = (pair i / P2, row
 // kyb = i % P2).  The row's N z-planes x LX values arrive by one 3-D tensor copy
@@ -636,7 +715,7 @@ __global__ void __launch_bounds__(NT, 2) k_pass_b_tma(const __grid_constant__ CU
     for (int b = 0; b < 2; ++b) {
       const int item = blockIdx.x + b * G;
       if (item < n_items) {
-        mbar_arrive_expect_tx(&bar[b], bytes);
+        mbar_arrive_expect_tx(&bar[b], bytes + (b == 0 && p.test_wait_expiry ? 16u : 0u));
         tma_load_3d(buf0 + b * BUF, &tm, 0, item % P2, (item / P2) * N, &bar[b]);
       }
     }
@@ -687,6 +766,50 @@ __global__ void __launch_bounds__(NT, 2) k_pass_b_tma(const __grid_constant__ CU
 // row buffers, the kept-f_z block
 template <int N> constexpr size_t smem_pass_b_tma(int LX, int P1, int P3) {
   return 128 + sizeof(float2) * ((size_t)2 * pass_b_tma_buf_elems<N>(LX) + (size_t)P3 * P1);
+}
+
+// Pass A, FP32, with the u_j planes staged: one CTA per SM of
+// PassASCfg::NT threads (one x-step item each) and one plane buffer; each
+// occupied band's plane z arrives in shared memory by one bulk copy, issued as
+// soon as the previous band's plane has been read (after the first x step), so
+// only u_a (the same plane for the whole loop, kept in L1) is read from global
+// memory.
+template <int N> using PassASCfg =
+    PlaneCfg<N, float, false, round_up(N * Lay<N>::A, lcm_c(lcm_c(32, Lay<N>::B), Lay<N>::A == 8 ? 1 : Lay<N>::A))>;
+template <int N>
+__global__ void __launch_bounds__(PassASCfg<N>::NT, 1) k_pass_a_staged(PairArgs p) {
+  using C = float2;
+  using G = PassASCfg<N>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int ok;
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* s0 = tw + N;
+  C* stage = s0 + G::BUF;
+  load_twiddles<N, float>(tw, p.tw);
+  __syncthreads();
+  const int ta = blockIdx.x, z = blockIdx.y;
+  constexpr long long plane = (long long)N * N;
+  const C* ua = reinterpret_cast<const C*>(p.u_tgt) + ta * p.u_tgt_stride + z * plane;
+  const C* uj0 = reinterpret_cast<const C*>(p.u_occ) + z * plane;
+  const int LX = p.LX;
+  PlaneStage st{&bar, &ok, stage, (unsigned)(plane * sizeof(C)), p.err};
+  st.start(uj0);
+#pragma unroll 1
+  for (int tj = 0; tj < p.TJ; ++tj) {
+    C* out = reinterpret_cast<C*>(p.inter) + ((long long)(ta * p.TJ + tj) * N + z) * (long long)p.P2 * LX;
+    const bool has_next = tj + 1 < p.TJ;
+    const C* next = has_next ? uj0 + (tj + 1) * p.u_occ_stride : nullptr;
+    if (!st.ready(tj)) return;
+    plane_forward<N, float, false, G::NT>(
+        tw, s0, s0, p.h1, p.P1, p.h2, [&](int y, int x) { return cmulc(stage[y * N + x], ua[y * N + x]); },
+        [&](int kyb, int kxb, C v) { out[kyb * LX + kxb] = v; }, [&] { st.issue(next); },
+        [&] { st.wait_next(tj, has_next); });
+  }
+}
+
+template <int N> constexpr size_t smem_pass_a_staged() {
+  return sizeof(float2) * ((size_t)N + (size_t)PassASCfg<N>::BUF + (size_t)N * N);
 }
 
 // Pass B for dE/dmu: forward z only, partial[pair][kyb] = sum dv/dmu/N^2 |rho|^2.

@@ -40,6 +40,12 @@ template <typename K> inline void allow_smem(K kernel, size_t bytes) {
 }
 
 template <int N, typename T> void launch_pass_a(const PairArgs& p, cudaStream_t s) {
+  if (sizeof(T) == 4 && p.stage_a) {
+    const size_t sm = smem_pass_a_staged<N>();
+    allow_smem(k_pass_a_staged<N>, sm);
+    k_pass_a_staged<N><<<dim3(p.TA, N), PassASCfg<N>::NT, sm, s>>>(p);
+    return;
+  }
   using G = PassACfg<N, T>;
   const size_t sm = G::smem();
   allow_smem(k_pass_a<N, T>, sm);

@@ -42,6 +42,9 @@ EXPORTS = ("xx_create", "xx_destroy", "xx_apply", "xx_apply_range", "xx_energy",
 XX_OPT_PAIR_SYMMETRY = 0
 XX_OPT_REAL_GAMMA = 1
 XX_OPT_TMA_PASS_B = 2
+XX_OPT_STAGE_PASS_A = 3
+XX_OPT_TEST_WAIT_EXPIRY = 4
+XX_OPT_FUSED_VJP = 5
 
 PROF_CLASSES = ("pass_a", "pass_b", "pass_c", "sphere_to_grid", "grid_to_sphere",
                 "kernel_table", "reduce", "pass_b_dmu")
@@ -335,6 +338,10 @@ class Plan:
     def set_tma_pass_b(self, mode: int):
         """0: one-row-per-block pass B; 1: automatic (default); 2: tensor-copy kernel."""
         xx_set_option(self.handle, XX_OPT_TMA_PASS_B, int(mode))
+
+    def set_stage_pass_a(self, mode: int):
+        """0: two CTAs per SM with global loads; 1: automatic (default); 2: staged."""
+        xx_set_option(self.handle, XX_OPT_STAGE_PASS_A, int(mode))
 
     def set_real_gamma(self, enable: bool):
         """Declare the orbitals of later calls real in real space (Gamma-only plans)."""

@@ -146,3 +146,27 @@ def test_dmu_pair_symmetry_matches_direct_pairs(gpu, prec, tol, make):
         out.append(float(dmu.item()))
         plan.close()
     assert abs(out[0] - out[1]) <= tol * abs(out[1])
+
+
+def test_device_copy_wait_expiry_is_reported(gpu):
+    """A tensor copy whose bounded wait runs out (the test option announces it 16 bytes
+    longer than it is) makes the CTA set the device flag and return: xx_sync reports
+    XX_ERR_DEVICE_FLAG, and the same context then computes a correct result."""
+    torch, xx = gpu
+    wl = synth.tiny_cubic()
+    c = gu.dev(wl.c_tgt)
+    wo, wt = gu.dev(wl.w_occ), gu.dev(wl.w_tgt)
+    plan = xx.Plan.from_workload(wl, precision=0)
+    plan.set_tma_pass_b(2)
+    xx.xx_set_option(plan.handle, xx.XX_OPT_TEST_WAIT_EXPIRY, 1)
+    plan.energy(c, wo, c, wt, shared=True)
+    with pytest.raises(xx.XXError) as ei:
+        plan.sync(timeout_s=120.0)
+    assert ei.value.status == -6            # XX_ERR_DEVICE_FLAG, cleared by the report
+    xx.xx_set_option(plan.handle, xx.XX_OPT_TEST_WAIT_EXPIRY, 0)
+    ex, vx = plan.energy(c, wo, c, wt, shared=True)
+    plan.sync(timeout_s=120.0)
+    ref, (e_ref, _), _ = gu.run(wl, 0)
+    assert gu.rel_max(vx.cpu().numpy(), ref) <= 1e-6
+    assert abs(float(ex[0].item()) - e_ref) <= 1e-6 * abs(e_ref)
+    plan.close()

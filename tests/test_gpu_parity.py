@@ -262,16 +262,18 @@ def test_pair_symmetry_transform_count(gpu):
 
 @pytest.mark.parametrize("make", [synth.tiny_cubic, rhombo24] +
                          [lambda i=i: synth.sweep_cell(i) for i in range(len(synth.SWEEP_GRIDS))])
-def test_tma_pass_b_matches_row_kernel(gpu, make):
-    """FP32 pass B staged by bulk tensor copies (forced on) against the one-row-per-block
-    kernel, on every grid length the sweep uses; ragged batches."""
+def test_staged_passes_match_unstaged(gpu, make):
+    """FP32 pass B staged by bulk tensor copies and pass A fed by bulk copies of the
+    occupied planes (both forced on) against the one-row-per-block pass B and the
+    global-load pass A, on every grid length the sweep uses; ragged batches."""
     torch, xx = gpu
     wl = make()
     out = []
-    for tma in (2, 0):
+    for tma, stage in ((2, True), (0, False)):
         plan = xx.Plan.from_workload(wl, precision=0)
         plan.set_batch(5, 3)
         plan.set_tma_pass_b(tma)
+        plan.set_stage_pass_a(2 if stage else 0)
         c = gu.dev(wl.c_tgt)
         ex, vx = plan.energy(c, gu.dev(wl.w_occ), c, gu.dev(wl.w_tgt), shared=True)
         plan.sync(timeout_s=600.0)
@@ -282,4 +284,6 @@ def test_tma_pass_b_matches_row_kernel(gpu, make):
     plan = xx.Plan.from_workload(wl, precision=0)
     with pytest.raises(xx.XXError):
         plan.set_tma_pass_b(3)
+    with pytest.raises(xx.XXError):
+        plan.set_stage_pass_a(-1)
     plan.close()

@@ -165,3 +165,25 @@ def test_real_gamma_option_needs_a_closed_gamma_basis(gpu):
     ok = xx.Plan.from_workload(wl, precision=0)
     ok.set_real_gamma(True)
     ok.close()
+
+
+@pytest.mark.parametrize("make", [synth.real_tiny_cubic, synth.real_alpha_cell])
+def test_real_gamma_staged_passes_match(gpu, make):
+    """The real-orbital path with pass A fed by bulk copies and the tensor-copy pass B
+    (forced on) against the unstaged kernels, FP32, odd tiles."""
+    torch, xx = gpu
+    wl = make()
+    out = []
+    for tma, stage in ((2, True), (0, False)):
+        plan = xx.Plan.from_workload(wl, precision=0)
+        plan.set_batch(5, 3)
+        plan.set_real_gamma(True)
+        plan.set_tma_pass_b(tma)
+        plan.set_stage_pass_a(2 if stage else 0)
+        ct = gu.dev(wl.c_tgt)
+        ex, vx = plan.energy(ct, gu.dev(wl.w_occ), ct, gu.dev(wl.w_tgt), shared=True)
+        plan.sync(timeout_s=600.0)
+        out.append((vx.cpu().numpy(), float(ex[0].item())))
+        plan.close()
+    assert gu.rel_max(out[0][0], out[1][0]) <= 1e-6
+    assert abs(out[0][1] - out[1][1]) <= 1e-6 * abs(out[1][1])

@@ -89,3 +89,24 @@ def test_autograd_apply_function(gpu, oracle_mod):
     assert gu.rel_max(c_tgt.grad.cpu().numpy(), 2 * gt) <= 1e-12
     assert gu.rel_max(c_occ.grad.cpu().numpy(), 2 * go) <= 1e-12
     plan.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-6), (1, 1e-12)])
+def test_fused_vjp_matches_separate_parts(gpu, prec, tol):
+    """Both gradients from two transforms per pair (default) against the target and
+    occupied parts computed by separate calls (three transforms per pair)."""
+    torch, xx = gpu
+    wl = rhombo24()
+    rng = np.random.default_rng(7)
+    ybar = masked_random(rng, wl, wl.c_tgt.shape)
+    fused = gpu_vjp(xx, wl, ybar, prec)
+    plan = xx.Plan.from_workload(wl, precision=prec)
+    xx.xx_set_option(plan.handle, xx.XX_OPT_FUSED_VJP, 0)
+    co, wo, ct, yb = gu.dev(wl.c_occ), gu.dev(wl.w_occ), gu.dev(wl.c_tgt), gu.dev(ybar)
+    gt, _ = plan.vjp(co, wo, ct, yb, want_occ=False)
+    _, go = plan.vjp(co, wo, ct, yb, want_tgt=False)
+    plan.sync(timeout_s=600.0)
+    sep = gt.cpu().numpy(), go.cpu().numpy()
+    plan.close()
+    assert gu.rel_max(fused[0], sep[0]) <= tol
+    assert gu.rel_max(fused[1], sep[1]) <= tol
