@@ -19,6 +19,7 @@ Printed as one JSON line (rank 0):
                 cell at the Gamma point only (real orbitals, 30,720 pairs)
   exact_grid    the same workload with the plan on the smallest grid on which the
                 operator is exact (60^3; same V_x c and E_x up to rounding)
+  alpha_boron   the alpha-boron-sized workload (48^3, 64 k-points, 1.77 M pairs)
   --impl reference  times the oracle as the reference arm.
 Multi-GPU (torchrun): each rank runs an independent workload (its own seed),
 weak scaling; value = all ranks' pairs / max-over-ranks time.
@@ -319,6 +320,41 @@ def exact_grid_leg(xx, torch, wl, stream, e_ref, reps=2):
                       "mean of %d steps" % (wl.name, n, 4 * int(wl.n_max().max()) + 1, reps)}
 
 
+def alpha_boron_leg(xx, torch, stream, hbm, reps=2):
+    """The alpha-boron-sized workload (48^3, MP 4x4x4 = 64 k-points, 18 occupied / 24
+    target bands: 1,769,472 pairs) through xx_energy with shared grids."""
+    from paper_1111_0716_gb300 import synth
+    wl = synth.alpha_boron()
+    plan = xx.Plan.from_workload(wl, precision=xx.XX_FP32_MIXED)
+    c = torch.from_numpy(wl.c_tgt).cuda()
+    wo = torch.from_numpy(wl.w_occ).cuda()
+    wt = torch.from_numpy(wl.w_tgt).cuda()
+    ex, vx = plan.energy(c, wo, c, wt, shared=True, stream=stream)
+    torch.cuda.synchronize()
+    p0 = plan.info()["pairs_transformed"]
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(reps):
+        plan.energy(c, wo, c, wt, vx_out=vx, ex_out=ex, shared=True, stream=stream)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    plan.sync(timeout_s=60.0, stream=stream)
+    info = plan.info()
+    t = g0.elapsed_time(g1) / 1e3 / reps
+    plan.close()
+    TA, TJ = info["targets_per_batch"], info["occupied_per_batch"]
+    sched = batch_schedule(wl.nk, wl.n_occ, wl.n_tgt, TA, TJ)
+    if sum(a * b for _, a, b in sched) * reps != info["pairs_transformed"] - p0:
+        raise RuntimeError("launch schedule model disagrees with the library (alpha-boron)")
+    path_bytes = sum(pass_bytes_per_step(wl, sched).values())
+    return {"value": wl.pair_count() / t, "unit": UNIT, "ms_per_step": 1e3 * t,
+            "path_roofline": {"achieved": path_bytes / t / 1e9, "peak": hbm, "unit": "GB/s",
+                              "frac": path_bytes / t / 1e9 / hbm},
+            "sample": "%s: 48^3, 64 k-points, 18 occupied x 24 targets = %d pairs, FP32-mixed, "
+                      "mean of %d steps" % (wl.name, wl.pair_count(), reps)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -333,6 +369,7 @@ def main():
     ap.add_argument("--no-real", action="store_true", help="skip the real-orbital Gamma leg")
     ap.add_argument("--no-exact-grid", action="store_true",
                     help="skip the smallest-exact-grid leg")
+    ap.add_argument("--no-alpha", action="store_true", help="skip the alpha-boron-sized leg")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one small slice of the workload (k=0, 16 targets, 32 occupied "
                          "bands, all q) once and exit: the case ncu captures")
@@ -543,6 +580,9 @@ def main():
 
     if rank == 0 and not args.no_exact_grid:
         line["exact_grid"] = exact_grid_leg(xx, torch, wl, stream, e_x)
+
+    if rank == 0 and not args.no_alpha:
+        line["alpha_boron"] = alpha_boron_leg(xx, torch, stream, hbm)
 
     if rank == 0 and args.with_vjp:
         nt = 16
