@@ -1,0 +1,66 @@
+"""Host logic of bench.py's roofline model, checked without a GPU.
+
+The launch schedule that bench.py rebuilds from the host loop must transform each
+band pair exactly once under the pair symmetry (every logical (k, a, q, j) pair is
+either transformed or the mirror of a transformed pair), and without the symmetry
+the per-pass byte model must reduce to the 48 bytes per grid point and logical pair
+of the plain three-pass pipeline plus its per-target terms.
+"""
+import itertools
+
+import pytest
+
+import bench
+
+
+def transformed_set(nk, n_occ, n_tgt, T):
+    """Pairs (k, a, q, j) the symmetric host loop transforms, by its rules."""
+    out = set()
+    for k, q, a, j in itertools.product(range(nk), range(nk), range(n_tgt), range(n_occ)):
+        if a >= n_occ:
+            out.add((k, a, q, j))                       # targets past the occupied set
+        elif q > k:
+            out.add((k, a, q, j))                       # blocks q > k, whole square
+        elif q == k and a // T <= j // T:
+            out.add((k, a, q, j))                       # k = q tiles I <= J
+    return out
+
+
+@pytest.mark.parametrize("nk,n_occ,n_tgt,TA,TJ", [(1, 8, 8, 3, 3), (3, 5, 7, 2, 4),
+                                                   (4, 6, 6, 4, 4), (2, 9, 12, 5, 3),
+                                                   (8, 4, 6, 3, 3)])
+def test_schedule_transforms_every_pair_once(nk, n_occ, n_tgt, TA, TJ):
+    T = min(TA, TJ)
+    tset = transformed_set(nk, n_occ, n_tgt, T)
+    sched = bench.batch_schedule(nk, n_occ, n_tgt, TA, TJ)
+    assert sum(ta * tj for _, ta, tj in sched) == len(tset)
+    # mirrored launches carry exactly the transformed pairs whose mirror is not
+    # transformed itself (tiles I < J and blocks q > k)
+    mirrored = sum(ta * tj for kind, ta, tj in sched if kind == "mirrored")
+    assert mirrored == sum(1 for (k, a, q, j) in tset
+                           if a < n_occ and (q, j, k, a) not in tset)
+    # every logical pair is covered exactly once
+    covered = set()
+    for (k, a, q, j) in tset:
+        assert (k, a, q, j) not in covered
+        covered.add((k, a, q, j))
+        if a < n_occ and (q, j, k, a) not in tset:
+            covered.add((q, j, k, a))
+    assert len(covered) == nk * n_tgt * nk * n_occ
+
+
+def test_byte_model_without_symmetry_is_48_bytes_per_point():
+    class W:                                    # the fields pass_bytes_per_step reads
+        grid = (24, 24, 24)
+    nk, n_occ, n_tgt, TA, TJ = 3, 10, 12, 5, 4
+    sched = bench.batch_schedule(nk, n_occ, n_tgt, TA, TJ, sym=False)
+    n3 = 24 ** 3
+    pairs = nk * n_tgt * nk * n_occ
+    assert sum(ta * tj for _, ta, tj in sched) == pairs
+    b = bench.pass_bytes_per_step(W, sched)
+    launches_per_target = nk * nk * -(-n_occ // TJ)       # (k, q, occupied batch) per target
+    per_target = n_tgt * launches_per_target
+    assert b["pass_a"] == 16 * n3 * pairs + 8 * n3 * per_target
+    assert b["pass_b"] == 16 * n3 * pairs
+    assert b["pass_c"] == 16 * n3 * pairs + 32 * n3 * per_target
+    assert sum(b.values()) == 48 * n3 * pairs + 40 * n3 * per_target
