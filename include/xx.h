@@ -275,8 +275,9 @@ int xx_sync(xx_plan plan, void *stream, double timeout_s);
                                    pair sums of dE_x/dmu and the strain derivative; in
                                    xx_apply / xx_energy over all k-points when FP64
                                    accumulators of every target of every k-point
-                                   (nk * n_tgt * N^3 * 16 bytes) fit in 64 GiB and can be
-                                   allocated, else both orders are transformed */
+                                   (nk * n_tgt * N^3 * 16 bytes) fit in XX_OPT_ACC_LIMIT_MB
+                                   (64 GiB) and can be allocated, else both orders are
+                                   transformed */
 #define XX_OPT_REAL_GAMMA 1     /* value != 0: the orbitals passed to later calls are real in
                                    real space (c(-G) = conj c(G) for every G of the basis), so
                                    every codensity is real and, at k = q = Gamma, so is every
@@ -322,9 +323,17 @@ int xx_sync(xx_plan plan, void *stream, double timeout_s);
                                    pair potential of (ubar_ka, u_qj) feeds both V_x ybar and the
                                    u_ka conj(Wbar) term of the occupied gradient.  Needs FP64
                                    accumulators of every occupied band of every k-point
-                                   (nk * n_occ * N^3 * 16 bytes, at most 64 GiB); otherwise,
+                                   (nk * n_occ * N^3 * 16 bytes, within XX_OPT_ACC_LIMIT_MB);
+                                   otherwise,
                                    or with 0, the two gradients are computed one after the
                                    other.  Results differ only by rounding order. */
+
+#define XX_OPT_ACC_LIMIT_MB 6   /* value >= 0: MiB of FP64 accumulators the plan may hold for
+                                   every k-point at once (the k != q pair symmetry of xx_apply
+                                   and xx_energy, the fused VJP); default 65536 (64 GiB).  Above
+                                   it those calls use per-k accumulators (k = q symmetry only,
+                                   VJP parts one after the other).  Negative values give
+                                   XX_ERR_INVALID_ARGUMENT. */
 
 /* Set a plan option; XX_ERR_INVALID_ARGUMENT for an unknown option. */
 int xx_set_option(xx_plan plan, int option, long long value);

@@ -283,6 +283,9 @@ struct xx_plan_s {
   int stage_pass_a = 1;        // XX_OPT_STAGE_PASS_A: 0 off, 1 for N <= 64, 2 always
   bool test_wait_expiry = false;   // XX_OPT_TEST_WAIT_EXPIRY
   bool fused_vjp = true;           // XX_OPT_FUSED_VJP
+  // XX_OPT_ACC_LIMIT_MB: MiB of FP64 accumulators held for every k-point at once
+  // (the k != q pair symmetry of xx_apply, the fused VJP); 64 GiB by default
+  long long acc_limit_mb = 64 << 10;
   int sm_count = 0;
   int tma_per_sm = -1;         // resident tensor-copy pass B CTAs per SM (-1: not queried)
   bool real_gamma = false;     // XX_OPT_REAL_GAMMA
@@ -313,9 +316,6 @@ struct xx_plan_s {
 namespace {
 
 const size_t kDefaultCap = (size_t)16 << 30;
-// FP64 accumulators of every target of every k-point, above which the k != q
-// pair symmetry of xx_apply is not used
-const size_t kCrossAccCap = (size_t)64 << 30;
 const int kGridChunk = 32;   // orbitals per sphere<->grid launch
 
 int cuda_status(cudaError_t e) {
@@ -716,7 +716,7 @@ int run_apply(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, const do
   // every k-point at once.
   const bool sym = shared && p->pair_symmetry && n_occ > 1;
   const size_t acc_k_bytes = (size_t)n_tgt * n3(p) * 16;
-  bool cross = sym && p->nk > 1 && (size_t)p->nk * acc_k_bytes <= kCrossAccCap;
+  bool cross = sym && p->nk > 1 && (size_t)p->nk * acc_k_bytes <= ((size_t)p->acc_limit_mb << 20);
   if (cross) {
     st = ensure(p, p->acc, (size_t)p->nk * acc_k_bytes);
     if (st == XX_ERR_OUT_OF_MEMORY)
@@ -1170,7 +1170,7 @@ int run_vjp_fused(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ,
                   cudaStream_t s) {
   const long long nn = n3(p);
   const size_t occ_bytes = (size_t)p->nk * n_occ * nn * 16;
-  if (occ_bytes > kCrossAccCap) return XX_ERR_OUT_OF_MEMORY;
+  if (occ_bytes > ((size_t)p->acc_limit_mb << 20)) return XX_ERR_OUT_OF_MEMORY;
   const bool shared = (c_occ == c_tgt && ld_occ == n_tgt);
   int st = build_grids(p, 0, p->nk, c_occ, ld_occ, n_occ, c_tgt, n_tgt, shared, s);
   if (st) return st;
@@ -1640,6 +1640,10 @@ int xx_set_option(xx_plan p, int option, long long value) {
     case XX_OPT_REAL_GAMMA:
       if (value != 0 && !p->gamma_closed) return XX_ERR_INVALID_ARGUMENT;
       p->real_gamma = value != 0;
+      return XX_OK;
+    case XX_OPT_ACC_LIMIT_MB:
+      if (value < 0) return XX_ERR_INVALID_ARGUMENT;
+      p->acc_limit_mb = value;
       return XX_OK;
     case XX_OPT_FUSED_VJP:
       p->fused_vjp = value != 0;

@@ -45,6 +45,7 @@ XX_OPT_TMA_PASS_B = 2
 XX_OPT_STAGE_PASS_A = 3
 XX_OPT_TEST_WAIT_EXPIRY = 4
 XX_OPT_FUSED_VJP = 5
+XX_OPT_ACC_LIMIT_MB = 6
 
 PROF_CLASSES = ("pass_a", "pass_b", "pass_c", "sphere_to_grid", "grid_to_sphere",
                 "kernel_table", "reduce", "pass_b_dmu")

@@ -287,3 +287,35 @@ def test_staged_passes_match_unstaged(gpu, make):
     with pytest.raises(xx.XXError):
         plan.set_stage_pass_a(-1)
     plan.close()
+
+
+def test_accumulator_limit_falls_back_to_per_k_accumulators(gpu):
+    """With no room for the accumulators of every k-point (XX_OPT_ACC_LIMIT_MB = 0)
+    the k != q blocks run in both orders and only the k = q tiles use the symmetry;
+    the result matches the default path and the one without symmetry (FP64)."""
+    torch, xx = gpu
+    wl = rhombo24()
+    out = []
+    for limit, sym in ((None, True), (0, True), (None, False)):
+        plan = xx.Plan.from_workload(wl, precision=1)
+        plan.set_batch(3, 3)
+        plan.set_pair_symmetry(sym)
+        if limit is not None:
+            xx.xx_set_option(plan.handle, xx.XX_OPT_ACC_LIMIT_MB, limit)
+        c = gu.dev(wl.c_tgt)
+        ex, vx = plan.energy(c, gu.dev(wl.w_occ), c, gu.dev(wl.w_tgt), shared=True)
+        plan.sync(timeout_s=600.0)
+        out.append((vx.cpu().numpy(), float(ex[0].item()), plan.info()["pairs_transformed"]))
+        plan.close()
+    for vx, e, _ in out[1:]:
+        assert gu.rel_max(vx, out[0][0]) <= 1e-12
+        assert abs(e - out[0][1]) <= 1e-12 * abs(out[0][1])
+    nk, no, nt = wl.nk, wl.n_occ, wl.n_tgt
+    diag = expected_transforms(1, no, nt, 3, 3, True)           # one k = q block
+    assert out[1][2] == nk * diag + (nk * nk - nk) * nt * no       # k != q in both orders
+    assert out[0][2] == expected_transforms(nk, no, nt, 3, 3, True)
+    assert out[2][2] == nk * nk * nt * no
+    plan = xx.Plan.from_workload(wl, precision=1)
+    with pytest.raises(xx.XXError):
+        xx.xx_set_option(plan.handle, xx.XX_OPT_ACC_LIMIT_MB, -1)
+    plan.close()

@@ -110,3 +110,20 @@ def test_fused_vjp_matches_separate_parts(gpu, prec, tol):
     plan.close()
     assert gu.rel_max(fused[0], sep[0]) <= tol
     assert gu.rel_max(fused[1], sep[1]) <= tol
+
+
+def test_fused_vjp_falls_back_without_room(gpu):
+    """XX_OPT_ACC_LIMIT_MB = 0 leaves no room for the occupied accumulators of every
+    k-point: xx_apply_vjp computes the two parts one after the other, same result."""
+    torch, xx = gpu
+    wl = rhombo24()
+    rng = np.random.default_rng(11)
+    ybar = masked_random(rng, wl, wl.c_tgt.shape)
+    fused = gpu_vjp(xx, wl, ybar, 1)
+    plan = xx.Plan.from_workload(wl, precision=1)
+    xx.xx_set_option(plan.handle, xx.XX_OPT_ACC_LIMIT_MB, 0)
+    gt, go = plan.vjp(gu.dev(wl.c_occ), gu.dev(wl.w_occ), gu.dev(wl.c_tgt), gu.dev(ybar))
+    plan.sync(timeout_s=600.0)
+    assert gu.rel_max(gt.cpu().numpy(), fused[0]) <= 1e-12
+    assert gu.rel_max(go.cpu().numpy(), fused[1]) <= 1e-12
+    plan.close()
