@@ -12,6 +12,7 @@
 // (with the pair symmetry, blocks q > k also feed the targets of q, and the
 // accumulators of every k-point are zeroed once up front)
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -316,6 +317,14 @@ struct xx_plan_s {
 namespace {
 
 const size_t kDefaultCap = (size_t)16 << 30;
+
+// NVTX range for timeline tools (nsys, ncu --nvtx); free when no tool is attached
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 const int kGridChunk = 32;   // orbitals per sphere<->grid launch
 
 int cuda_status(cudaError_t e) {
@@ -405,6 +414,7 @@ void prof_end(xx_plan p, int cls, int e0, cudaStream_t s) {
 
 // sphere -> grid for nb orbitals of k-point k: c[b][npw_max] -> u[b][N^3]
 int sphere_to_grid(xx_plan p, int k, const double2* c, int nb, void* u, cudaStream_t s) {
+  Range r("xx sphere->grid");
   const size_t eb = elem_bytes(p);
   const int Q1 = Q(p, 0), Q2 = Q(p, 1), Q3 = Q(p, 2);
   const int chunk = nb < kGridChunk ? nb : kGridChunk;
@@ -449,6 +459,7 @@ int sphere_to_grid(xx_plan p, int k, const double2* c, int nb, void* u, cudaStre
 
 // grid -> sphere for nb FP64 grids f[b][N^3] of k-point k into out[b][npw_max]
 int grid_to_sphere(xx_plan p, int k, const double2* f, int nb, double2* out, cudaStream_t s) {
+  Range r("xx grid->sphere");
   const int Q1 = Q(p, 0), Q2 = Q(p, 1), Q3 = Q(p, 2);
   const int chunk = nb < kGridChunk ? nb : kGridChunk;
   int st = ensure(p, p->box, (size_t)chunk * Q1 * Q2 * Q3 * 16);
@@ -730,6 +741,9 @@ int run_apply(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, const do
   const int T = TJ < TA ? TJ : TA;
   for (int kk = 0; kk < kn; ++kk) {
     const int k = k0 + kk;
+    char name[32];
+    std::snprintf(name, sizeof(name), "xx target k-point %d", k);
+    Range r(name);
     double2* acc_k = (double2*)p->acc.p + (cross ? k * acc_k_elems : 0);
     if (!cross) cudaMemsetAsync(acc_k, 0, acc_k_bytes, s);
     for (int q = 0; q < p->nk; ++q) {
@@ -949,6 +963,7 @@ int run_pair_sums_real(xx_plan p, const void* c, const double* w, int n_b, bool 
 
 int run_energy_reduce(xx_plan p, int k0, int kn, const void* c_tgt, const double* w_tgt, int n_tgt,
                       const void* vx, double* ex_out, cudaStream_t s) {
+  Range r("xx E_x reduction");
   const int rows = kn * n_tgt;
   int st = ensure(p, p->dots, (size_t)rows * 16);
   if (st) return st;
@@ -963,6 +978,7 @@ int run_energy_reduce(xx_plan p, int k0, int kn, const void* c_tgt, const double
 // dE/dmu accumulation: codensities recomputed (pass A) + forward z with dv/dmu (pass B')
 int run_dmu(xx_plan p, const void* c, const double* w, int n_b, double grad, double* dmu_out,
             cudaStream_t s) {
+  Range r("xx dE/dmu");
   const double factor = -0.5 * kSpin * p->omega / ((double)p->nk * (double)p->nk) * grad;
   int st;
   if (p->real_gamma) {
@@ -1050,6 +1066,7 @@ int strain_tables(xx_plan p, int k, int q, cudaStream_t s) {
 
 int run_strain(xx_plan p, const void* c, const double* w, int n_b, double* out9, double* ex_out,
                cudaStream_t s) {
+  Range r("xx strain derivative");
   int st = ensure(p, p->dmu_acc, 7 * 8);
   if (st) return st;
   cudaMemsetAsync(p->dmu_acc.p, 0, 7 * 8, s);
@@ -1401,6 +1418,7 @@ namespace {
 int apply_range(xx_plan p, int k_first, int k_count, const void* c_occ, int ld_occ,
                 const double* w_occ, int n_occ, const void* c_tgt, int n_tgt, void* vx_out,
                 bool real, void* stream) {
+  Range r("xx apply");
   if (!p || n_occ < 0 || n_tgt < 0 || k_first < 0 || k_count < 0 || k_first + k_count > p->nk)
     return XX_ERR_INVALID_ARGUMENT;
   if (ld_occ == 0) ld_occ = n_occ;
@@ -1560,6 +1578,7 @@ int xx_run_many(int n_jobs, const xx_job* jobs, void* stream) {
 int xx_apply_vjp(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, int n_occ,
                  const void* c_tgt, int n_tgt, const void* ybar, void* grad_tgt_out,
                  void* grad_occ_out, void* stream) {
+  Range r("xx vjp");
   if (!p || n_occ < 0 || n_tgt < 0) return XX_ERR_INVALID_ARGUMENT;
   if (ld_occ == 0) ld_occ = n_occ;
   if (ld_occ < n_occ) return XX_ERR_INVALID_ARGUMENT;

@@ -631,11 +631,11 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
       : "memory");
 }
 
-// Shared staging of the pair-intermediate planes read by pass C (one plane of
-// P2 x LX values per loop step, contiguous in global memory): the plane of step
-// s + 1 is copied in by one bulk copy issued as soon as step s has read its
-// plane (after the first y step), and waited for before step s ends.  All waits
-// are bounded; a wait that runs out makes every thread leave (ok == 0).
+// Shared staging of one contiguous plane per loop step (pass A: the occupied
+// orbital's plane z): the plane of step s + 1 is copied in by one bulk copy
+// issued as soon as step s has read its plane, and waited for before step s
+// ends.  All waits are bounded; a wait that runs out makes every thread leave
+// (ok == 0).
 struct PlaneStage {
   uint64_t* bar;
   int* ok;

@@ -319,3 +319,21 @@ def test_accumulator_limit_falls_back_to_per_k_accumulators(gpu):
     with pytest.raises(xx.XXError):
         xx.xx_set_option(plan.handle, xx.XX_OPT_ACC_LIMIT_MB, -1)
     plan.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, gu.FP32_TOL), (1, gu.FP64_TOL)])
+def test_grid_64_k_mesh(gpu, oracle_mod, prec, tol):
+    """The one supported FFT length no other workload uses (64 = 8 x 8): a cubic
+    cell with a 2x2x2 MP mesh and targets past the occupied set, sampled targets
+    against the oracle and Hermiticity on every k-point."""
+    wl = synth.make_workload("cubic64", synth.cubic_lattice(10.0 * 64 / 24), (64,) * 3,
+                             synth.monkhorst_pack(2), math.pi, 6, 8,
+                             [1.0, 1.0, 1.0, 1.0, 0.5, 0.25], 64)
+    assert np.all(4 * wl.n_max() + 1 <= 64)
+    vx, (e, e_im), _ = gu.run(wl, prec)
+    sel = [(0, 0), (wl.nk - 1, wl.n_tgt - 1), (3, 5)]
+    ref = oracle_mod.apply(wl, sel=sel)
+    got = np.stack([vx[k, a] for k, a in sel])
+    assert gu.rel_max(got, ref) <= tol
+    assert gu.hermitian_defect(wl.c_tgt, vx) <= max(tol, 1e-12)
+    assert abs(e_im) <= max(tol, 1e-12) * abs(e)

@@ -187,3 +187,24 @@ def test_real_gamma_staged_passes_match(gpu, make):
         plan.close()
     assert gu.rel_max(out[0][0], out[1][0]) <= 1e-6
     assert abs(out[0][1] - out[1][1]) <= 1e-6 * abs(out[1][1])
+
+
+def test_real_gamma_negative_occupation_sets_the_device_flag(gpu):
+    """A negative occupation on the real path (it folds sqrt(w) into the packed slots
+    for dE/dmu) is caught on the device: the flag is set, xx_sync reports
+    XX_ERR_DEVICE_FLAG and clears it, and the context stays usable."""
+    torch, xx = gpu
+    wl = synth.real_tiny_cubic()
+    w_bad = wl.w_tgt.copy()
+    w_bad[0, 1] = -0.5
+    plan = xx.Plan.from_workload(wl, precision=1)
+    plan.set_real_gamma(True)
+    ct = gu.dev(wl.c_tgt)
+    plan.backward(ct, gu.dev(w_bad), grad_ex=1.0, want_dc=False)
+    with pytest.raises(xx.XXError) as ei:
+        plan.sync(timeout_s=120.0)
+    assert ei.value.status == -6
+    _, dmu = plan.backward(ct, gu.dev(wl.w_tgt), grad_ex=1.0, want_dc=False)
+    plan.sync(timeout_s=120.0)
+    assert np.isfinite(float(dmu.item()))
+    plan.close()
