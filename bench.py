@@ -231,8 +231,10 @@ def profile_case(args):
         # the first two k-points with shared grids: k = q tiles, the pair-symmetric
         # block (0, 1) (passes A, B, C and the role-swapped pass C at 64 x 80) and
         # the targets past the occupied set
+        nb = 16 if args.profile_small else wl.coeff.shape[1]
         sub = wl.replace(kfrac=wl.kfrac[:2], npw=wl.npw[:2], miller=wl.miller[:2],
-                         coeff=wl.coeff[:2], w=wl.w[:2])
+                         coeff=wl.coeff[:2, :nb], w=wl.w[:2, :nb], n_occ=min(wl.n_occ, nb),
+                         n_tgt=min(wl.n_tgt, nb))
         plan = xx.Plan.from_workload(sub, precision=prec)
         c = torch.from_numpy(sub.c_tgt).cuda()
         ex, vx = plan.energy(c, torch.from_numpy(sub.w_occ).cuda(), c,
@@ -377,7 +379,8 @@ def main():
                     help="precision of --profile-case")
     ap.add_argument("--profile-small", action="store_true",
                     help="with --profile-case: 16 targets x 16 occupied bands (a few GB on the "
-                         "device, for multi-pass ncu captures)")
+                         "device, for multi-pass ncu captures); with --profile-shared: 16 bands "
+                         "at each of the two k-points")
     ap.add_argument("--profile-shared", action="store_true",
                     help="with --profile-case: xx_energy on the first two k-points with shared "
                          "grids (pair-symmetric batches, role-swapped pass C; about 25 GB)")
