@@ -130,29 +130,48 @@ def recorded_traffic(kernel, batch):
     return d.get("bytes_per_launch", {}).get(kernel)
 
 
-def batch_schedule(nk, n_occ, n_tgt, TA, TJ, sym=True, cross=True):
+def batch_schedule(nk, n_occ, n_tgt, TA, TJ, G_max=1, sym=True, cross=True):
     """The band-pair launches of one xx_energy call with shared grids, in the
     host loop's order: (kind, targets, occupied) with kind "full" (passes A, B,
-    C) or "mirrored" (passes A, B, C and the role-swapped pass C)."""
+    C) or "mirrored" (passes A, B, C and the role-swapped pass C).  G_max is the
+    plan's q_per_batch: that many k-points' whole occupied sets share a batch;
+    target batches are cut at n_occ (the split of the grids' layout)."""
     out = []
     T = min(TA, TJ)
+    sym = sym and n_occ > 1
+
+    def run_q(q_lo, q_hi, a_lo, a_hi, mirrored):
+        if a_lo >= a_hi:
+            return
+        q0 = q_lo
+        while q0 < q_hi:
+            G = min(G_max, q_hi - q0)
+            cut = n_occ if a_lo < n_occ < a_hi else a_hi
+            for lo, hi in ((a_lo, cut), (cut, a_hi)):
+                for a0 in range(lo, hi, TA):
+                    ta = min(TA, hi - a0)
+                    jstep = n_occ if G > 1 else TJ
+                    for j0 in range(0, n_occ, jstep):
+                        nj = min(jstep, n_occ - j0)
+                        out.append(("mirrored" if mirrored else "full", ta, G * nj))
+            q0 += G
+
     for k in range(nk):
-        for q in range(nk):
-            diag = sym and q == k
-            upper = sym and cross and q > k
-            lower = sym and cross and q < k
-            if diag:
-                for i0 in range(0, n_occ, T):
-                    for j0 in range(i0, n_occ, T):
-                        out.append(("mirrored" if j0 > i0 else "full",
-                                    min(T, n_occ - i0), min(T, n_occ - j0)))
-            if upper:
-                for a0 in range(0, n_occ, TA):
-                    for j0 in range(0, n_occ, TJ):
-                        out.append(("mirrored", min(TA, n_occ - a0), min(TJ, n_occ - j0)))
-            for a0 in range(n_occ if (diag or upper or lower) else 0, n_tgt, TA):
-                for j0 in range(0, n_occ, TJ):
-                    out.append(("full", min(TA, n_tgt - a0), min(TJ, n_occ - j0)))
+        if not sym:
+            run_q(0, nk, 0, n_tgt, False)
+            continue
+        for i0 in range(0, n_occ, T):
+            for j0 in range(i0, n_occ, T):
+                out.append(("mirrored" if j0 > i0 else "full", min(T, n_occ - i0),
+                            min(T, n_occ - j0)))
+        run_q(k, k + 1, n_occ, n_tgt, False)
+        if cross:
+            run_q(0, k, n_occ, n_tgt, False)
+            run_q(k + 1, nk, 0, n_occ, True)
+            run_q(k + 1, nk, n_occ, n_tgt, False)
+        else:
+            run_q(0, k, 0, n_tgt, False)
+            run_q(k + 1, nk, 0, n_tgt, False)
     return out
 
 
@@ -346,7 +365,7 @@ def alpha_boron_leg(xx, torch, stream, hbm, reps=2):
     t = g0.elapsed_time(g1) / 1e3 / reps
     plan.close()
     TA, TJ = info["targets_per_batch"], info["occupied_per_batch"]
-    sched = batch_schedule(wl.nk, wl.n_occ, wl.n_tgt, TA, TJ)
+    sched = batch_schedule(wl.nk, wl.n_occ, wl.n_tgt, TA, TJ, info["q_per_batch"])
     if sum(a * b for _, a, b in sched) * reps != info["pairs_transformed"] - p0:
         raise RuntimeError("launch schedule model disagrees with the library (alpha-boron)")
     path_bytes = sum(pass_bytes_per_step(wl, sched).values())
@@ -501,7 +520,7 @@ def main():
     # device time during the timed steps, against the measured HBM copy rate
     hbm, peak_kind = peaks()
     TA, TJ = info["targets_per_batch"], info["occupied_per_batch"]
-    sched = batch_schedule(wl.nk, wl.n_occ, wl.n_tgt, TA, TJ)
+    sched = batch_schedule(wl.nk, wl.n_occ, wl.n_tgt, TA, TJ, info["q_per_batch"])
     transformed = sum(ta * tj for _, ta, tj in sched)
     if transformed * args.steps != pairs_step_transformed:
         raise RuntimeError("launch schedule model (%d pairs) disagrees with the library (%d)"

@@ -94,6 +94,9 @@ typedef struct {
   long long pairs_transformed; /* band pairs (or packed slots) that went through the
                                   codensity transform so far; below the logical pair
                                   count when the pair symmetry is used */
+  int q_per_batch;          /* k-points whose whole occupied sets share one band-pair batch
+                               in the last xx_apply / xx_energy (1 unless a k-point has at
+                               most half as many occupied bands as the default batch width) */
 } xx_info;
 
 /*
@@ -105,7 +108,8 @@ typedef struct {
  * band-pair intermediate in bytes (0 = 16 GiB); it sets how many band pairs are
  * processed per batch (the paper's NSIM control of GPU memory): the default
  * batch of 64 targets x 80 occupied bands is halved (occupied first) until its
- * intermediate fits.
+ * intermediate fits.  When a k-point has at most half as many occupied bands as
+ * the batch is wide, the occupied sets of consecutive k-points share a batch.
  * Returns XX_ERR_INVALID_ARGUMENT, XX_ERR_UNSUPPORTED_GRID, XX_ERR_GRID_ALIASING,
  * XX_ERR_NO_DEVICE, XX_ERR_OUT_OF_MEMORY or XX_OK; *out is NULL on failure.
  */

@@ -291,7 +291,12 @@ struct xx_plan_s {
   int tma_per_sm = -1;         // resident tensor-copy pass B CTAs per SM (-1: not queried)
   bool real_gamma = false;     // XX_OPT_REAL_GAMMA
   bool gamma_closed = false;   // one k-point at Gamma whose basis holds -G for every G
-  int ta_last = 0, tj_last = 0;
+  int ta_last = 0, tj_last = 0, g_last = 1;
+  // Layout of the shared orbital grids (occupied = leading target bands): the
+  // occupied bands of every k-point first ([nk][split]), then the remaining
+  // targets ([nk][n_tgt - split]), so the occupied grids of consecutive
+  // k-points are contiguous; split = 0: plain [k][n_tgt]
+  int split = 0, split_nk = 0, split_ntgt = 0;
   const KernelTable* kt = nullptr;
   int* d_miller = nullptr;   // [nk][npw_max][3]
   int* d_npw = nullptr;      // [nk]
@@ -317,6 +322,7 @@ struct xx_plan_s {
 namespace {
 
 const size_t kDefaultCap = (size_t)16 << 30;
+const int kDefaultTA = 64, kDefaultTJ = 80;   // band-pair batch (targets x occupied)
 
 // NVTX range for timeline tools (nsys, ncu --nvtx); free when no tool is attached
 struct Range {
@@ -497,12 +503,14 @@ int grid_to_sphere(xx_plan p, int k, const double2* f, int nb, double2* out, cud
   return XX_OK;
 }
 
-int kernel_table_for(xx_plan p, int k, int q, bool with_dmu, cudaStream_t s) {
+// v(k - q + G)/N (and dv/dmu/N^2) over the pruned box into table slot `slot` of
+// `slots` (each P1 P2 P3 values); the buffers are sized for every slot first
+int kernel_table_for(xx_plan p, int k, int q, bool with_dmu, cudaStream_t s, int slot = 0, int slots = 1) {
   const size_t eb = p->prec == XX_FP64 ? 8 : 4;
   const long long nbox = (long long)P(p, 0) * P(p, 1) * P(p, 2);
-  int st = ensure(p, p->vt, nbox * eb);
+  int st = ensure(p, p->vt, (size_t)slots * nbox * eb);
   if (st) return st;
-  if (with_dmu && (st = ensure(p, p->dvt, nbox * eb))) return st;
+  if (with_dmu && (st = ensure(p, p->dvt, (size_t)slots * nbox * eb))) return st;
   VtabArgs a{};
   std::memcpy(a.M, p->M, sizeof(a.M));
   for (int i = 0; i < 3; ++i) a.d[i] = p->kfrac[3 * k + i] - p->kfrac[3 * q + i];
@@ -519,9 +527,11 @@ int kernel_table_for(xx_plan p, int k, int q, bool with_dmu, cudaStream_t s) {
   const int blocks = (int)((nbox + 255) / 256);
   const int e = prof_begin(p, s);
   if (p->prec == XX_FP64)
-    k_vtab<double><<<blocks, 256, 0, s>>>((double*)p->vt.p, with_dmu ? (double*)p->dvt.p : nullptr, a);
+    k_vtab<double><<<blocks, 256, 0, s>>>((double*)p->vt.p + slot * nbox,
+                                          with_dmu ? (double*)p->dvt.p + slot * nbox : nullptr, a);
   else
-    k_vtab<float><<<blocks, 256, 0, s>>>((float*)p->vt.p, with_dmu ? (float*)p->dvt.p : nullptr, a);
+    k_vtab<float><<<blocks, 256, 0, s>>>((float*)p->vt.p + slot * nbox,
+                                         with_dmu ? (float*)p->dvt.p + slot * nbox : nullptr, a);
   prof_end(p, XX_PROF_KERNEL_TABLE, e, s);
   return launched(p, 1);
 }
@@ -531,8 +541,8 @@ void batch_shape(xx_plan p, int n_tgt, int n_occ, int* TA, int* TJ) {
   // 64 x 80 measured best on the 96^3 workload: a long occupied loop amortises
   // pass C's prologue and FP64 accumulator update, and 6144 CTAs per launch
   // keep the last wave short
-  int ta = p->ta_user > 0 ? p->ta_user : 64;
-  int tj = p->tj_user > 0 ? p->tj_user : 80;
+  int ta = p->ta_user > 0 ? p->ta_user : kDefaultTA;
+  int tj = p->tj_user > 0 ? p->tj_user : kDefaultTJ;
   if (ta > n_tgt) ta = n_tgt;
   if (tj > n_occ) tj = n_occ;
   while ((size_t)ta * tj * per_pair > p->cap && tj > 1) tj = (tj + 1) / 2;
@@ -562,6 +572,7 @@ PairArgs pair_args(xx_plan p, int TA, int TJ) {
   a.coef = -1.0 / (double)p->nk;
   a.err = p->d_err;
   a.test_wait_expiry = p->test_wait_expiry ? 1 : 0;
+  a.nj = TJ;   // one q-point per occupied batch unless the caller sets segments
   // measured on GB300 (beta cell, 64 targets x 160 occupied x 8 q, pass A): staged
   // 5.6 % faster at N = 60, 13 % slower at N = 96 (one CTA of 768 threads per SM
   // against two of 384)
@@ -571,17 +582,36 @@ PairArgs pair_args(xx_plan p, int TA, int TJ) {
 
 bool bad_ptr(const void* a) { return a == nullptr; }
 
+// Index of band b of k-point k in a split layout of nk k-points: the first
+// `split` bands of every k-point, then the other n_b - split (split = 0: plain).
+long long split_index(int split, int nk, int n_b, int k, int b) {
+  if (split <= 0) return (long long)k * n_b + b;
+  if (b < split) return (long long)k * split + b;
+  return (long long)nk * split + (long long)k * (n_b - split) + (b - split);
+}
+
 // Grids of targets (and occupied, unless shared) for every k.
 // Targets of k-points k0..k0+kn-1 (c_tgt holds only those), occupied of every q.
+// Shared grids use the split layout (occupied bands of every k-point first).
 int build_grids(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, int n_occ,
                 const void* c_tgt, int n_tgt, bool shared, cudaStream_t s) {
   const size_t eb = elem_bytes(p);
   int st = ensure(p, p->u_tgt, (size_t)kn * n_tgt * n3(p) * eb);
   if (st) return st;
+  p->split = shared && n_occ < n_tgt ? n_occ : 0;
+  p->split_nk = kn;
+  p->split_ntgt = n_tgt;
   for (int kk = 0; kk < kn; ++kk) {
-    st = sphere_to_grid(p, k0 + kk, (const double2*)c_tgt + (long long)kk * n_tgt * p->npw_max, n_tgt,
-                        (char*)p->u_tgt.p + (size_t)kk * n_tgt * n3(p) * eb, s);
-    if (st) return st;
+    const double2* ck = (const double2*)c_tgt + (long long)kk * n_tgt * p->npw_max;
+    const int parts = p->split > 0 ? 2 : 1;
+    for (int part = 0; part < parts; ++part) {
+      const int b0 = part == 0 ? 0 : p->split;
+      const int nb = parts == 1 ? n_tgt : (part == 0 ? p->split : n_tgt - p->split);
+      const long long idx = split_index(p->split, kn, n_tgt, kk, b0);
+      st = sphere_to_grid(p, k0 + kk, ck + (long long)b0 * p->npw_max, nb,
+                          (char*)p->u_tgt.p + (size_t)idx * n3(p) * eb, s);
+      if (st) return st;
+    }
   }
   if (!shared) {
     if ((st = ensure(p, p->u_occ, (size_t)p->nk * n_occ * n3(p) * eb))) return st;
@@ -594,9 +624,12 @@ int build_grids(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, int n_
   return XX_OK;
 }
 
+// grid of band j of k-point q: shared = in the target grids (split layout),
+// else in the separate occupied grids [nk][n_occ]
 const char* grid_ptr(xx_plan p, bool shared, int q, int j, int n_occ, int n_tgt) {
   const size_t eb = elem_bytes(p);
-  if (shared) return (const char*)p->u_tgt.p + ((size_t)q * n_tgt + j) * n3(p) * eb;
+  if (shared)
+    return (const char*)p->u_tgt.p + (size_t)split_index(p->split, p->split_nk, n_tgt, q, j) * n3(p) * eb;
   return (const char*)p->u_occ.p + ((size_t)q * n_occ + j) * n3(p) * eb;
 }
 
@@ -679,28 +712,42 @@ void run_pass_ct(xx_plan p, const PairArgs& a, cudaStream_t s) {
   prof_end(p, XX_PROF_PASS_C, e, s);
 }
 
-// One transformed batch of the pair-symmetric path: targets a0.. (ta of them)
-// of k-point k against occupied bands j0.. (tj) of q.  Pass C adds
-// -(w_qj/N_k) u_qj W_aj into the accumulators of the targets (acc_a); with
-// acc_j set, the role-swapped pass C adds -(w_ka/N_k) u_ka conj(W_aj) into the
-// accumulators of the targets (q, j0..) (W_qj,ka = conj(W_ka,qj)).  The grids
-// are the shared ones of every k-point.
-int sym_batch(xx_plan p, int k, int a0, int ta, int q, int j0, int tj, int n_occ, int n_tgt,
-              const double* w_occ, double2* acc_a, double2* acc_j, cudaStream_t s) {
-  PairArgs a = pair_args(p, ta, tj);
-  a.u_tgt = grid_ptr(p, true, k, a0, n_occ, n_tgt);
-  a.u_occ = grid_ptr(p, true, q, j0, n_occ, n_tgt);
-  a.acc = acc_a;
-  a.w_occ = w_occ + (long long)q * n_occ + j0;
+// One band-pair batch: targets a0.. (ta of them, grids u_tgt consecutive) of
+// k-point k against an occupied batch of G segments, one per k-point q0, q0+1,
+// .., of nj bands each (G > 1 only with whole occupied sets), whose grids
+// (u_occ), occupations (w_occ) and role-swapped accumulators (acc_j) are
+// consecutive across the segments; kernel tables of the G q-points in slots
+// 0..G-1.  Pass C adds -(w_qj/N_k) u_qj W_aj into the accumulators acc_a of the
+// targets; with acc_j set, the role-swapped pass C adds -(w_ka/N_k) u_ka
+// conj(W_aj) into them (W_qj,ka = conj(W_ka,qj)).
+struct SegBatch {
+  const char* u_tgt = nullptr;
+  int ta = 0;
+  const char* u_occ = nullptr;
+  int G = 1, nj = 0;
+  const double* w_occ = nullptr;
+  double2* acc_a = nullptr;
+  double2* acc_j = nullptr;
+  const double* w_tgt = nullptr;   // occupations of the targets (role-swapped pass C)
+};
+
+int seg_batch(xx_plan p, const SegBatch& b, cudaStream_t s) {
+  PairArgs a = pair_args(p, b.ta, b.G * b.nj);
+  a.u_tgt = b.u_tgt;
+  a.u_occ = b.u_occ;
+  a.nj = b.nj;
+  a.vt_seg = (long long)P(p, 0) * P(p, 1) * P(p, 2);
+  a.acc = b.acc_a;
+  a.w_occ = b.w_occ;
   run_pass_a(p, a, s);
   run_pass_b(p, a, s);
   run_pass_c(p, a, s);
   int nl = 3;
-  if (acc_j) {
+  if (b.acc_j) {
     PairArgs c = a;
-    c.w_tgt = w_occ + (long long)k * n_occ + a0;
+    c.w_tgt = b.w_tgt;
     c.w_occ = nullptr;
-    c.acc = acc_j;
+    c.acc = b.acc_j;
     run_pass_ct(p, c, s);
     ++nl;
   }
@@ -716,17 +763,28 @@ int run_apply(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, const do
   if (st) return st;
   int TA, TJ;
   batch_shape(p, n_tgt, n_occ, &TA, &TJ);
+  // An occupied batch spans G_max consecutive q-points when a q-point's whole
+  // occupied set fits the batch width at least twice (few bands, many k-points):
+  // fewer, wider launches.
+  const int tj_cap = p->tj_user > 0 ? p->tj_user : kDefaultTJ;
+  int G_max = 1;
+  if (n_occ > 0 && 2 * n_occ <= tj_cap) {
+    G_max = tj_cap / n_occ < p->nk ? tj_cap / n_occ : p->nk;
+    while (G_max > 1 && (size_t)TA * G_max * n_occ * inter_pair_bytes(p) > p->cap) --G_max;
+  }
   p->ta_last = TA;
   p->tj_last = TJ;
-  const size_t eb = elem_bytes(p);
-  if ((st = ensure(p, p->inter, (size_t)TA * TJ * inter_pair_bytes(p)))) return st;
+  p->g_last = G_max;
+  const long long nn = n3(p);
+  const int TJb = G_max > 1 ? G_max * n_occ : TJ;   // occupied columns of the widest batch
+  if ((st = ensure(p, p->inter, (size_t)TA * TJb * inter_pair_bytes(p)))) return st;
   // Pair symmetry: with the occupied grids shared with the leading targets,
   // W_qj,ka = conj(W_ka,qj) (v(q - k + G) = v(k - q - G)).  On k = q blocks the
   // occupied square is tiled and only tiles I <= J are transformed; across
   // k-points (cross) only blocks q > k are, which needs the accumulators of
-  // every k-point at once.
+  // every k-point at once (in the split layout of the grids).
   const bool sym = shared && p->pair_symmetry && n_occ > 1;
-  const size_t acc_k_bytes = (size_t)n_tgt * n3(p) * 16;
+  const size_t acc_k_bytes = (size_t)n_tgt * nn * 16;
   bool cross = sym && p->nk > 1 && (size_t)p->nk * acc_k_bytes <= ((size_t)p->acc_limit_mb << 20);
   if (cross) {
     st = ensure(p, p->acc, (size_t)p->nk * acc_k_bytes);
@@ -736,66 +794,103 @@ int run_apply(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, const do
       return st;
   }
   if (!cross && (st = ensure(p, p->acc, acc_k_bytes))) return st;
-  const long long acc_k_elems = (long long)n_tgt * n3(p);
   if (cross) cudaMemsetAsync(p->acc.p, 0, (size_t)p->nk * acc_k_bytes, s);
+  const int split = cross ? p->split : 0;
+  // accumulator of band b of k-point k (targets of one k when not cross)
+  auto acc_ptr = [&](int k, int b) -> double2* {
+    if (!cross) return (double2*)p->acc.p + (long long)b * nn;
+    return (double2*)p->acc.p + split_index(split, p->nk, n_tgt, k, b) * nn;
+  };
   const int T = TJ < TA ? TJ : TA;
   for (int kk = 0; kk < kn; ++kk) {
     const int k = k0 + kk;
-    char name[32];
+    char name[40];
     std::snprintf(name, sizeof(name), "xx target k-point %d", k);
     Range r(name);
-    double2* acc_k = (double2*)p->acc.p + (cross ? k * acc_k_elems : 0);
-    if (!cross) cudaMemsetAsync(acc_k, 0, acc_k_bytes, s);
-    for (int q = 0; q < p->nk; ++q) {
-      const bool diag = sym && q == k;
-      const bool upper = cross && q > k;   // occupied square, both directions
-      const bool lower = cross && q < k;   // occupied square done by block (q, k)
-      const int a_first = (diag || upper || lower) ? n_occ : 0;
-      if (lower && a_first >= n_tgt) continue;
-      if ((st = kernel_table_for(p, k, q, false, s))) return st;
-      if (diag) {
-        for (int i0 = 0; i0 < n_occ; i0 += T) {
-          const int ti = (n_occ - i0) < T ? (n_occ - i0) : T;
-          for (int j0 = i0; j0 < n_occ; j0 += T) {
-            const int tj = (n_occ - j0) < T ? (n_occ - j0) : T;
-            // tiles J > I: targets of tile J receive -(w_a/N_k) u_a conj(W_aj)
-            st = sym_batch(p, k, i0, ti, q, j0, tj, n_occ, n_tgt, w_occ, acc_k + (long long)i0 * n3(p),
-                           j0 > i0 ? acc_k + (long long)j0 * n3(p) : nullptr, s);
-            if (st) return st;
+    if (!cross) cudaMemsetAsync(p->acc.p, 0, acc_k_bytes, s);
+    // targets [a_lo, a_hi) of k (cut at n_occ, where the split layout jumps)
+    // against the occupied sets of the q-points [q_lo, q_hi), in segments of up
+    // to G_max q-points; mirrored: the role-swapped pass C too (blocks q > k)
+    auto run_q = [&](int q_lo, int q_hi, int a_lo, int a_hi, bool mirrored) -> int {
+      if (a_lo >= a_hi) return XX_OK;
+      for (int q0 = q_lo; q0 < q_hi;) {
+        const int G = (q_hi - q0) < G_max ? (q_hi - q0) : G_max;
+        for (int g = 0; g < G; ++g) {
+          const int e = kernel_table_for(p, k, q0 + g, false, s, g, G);
+          if (e) return e;
+        }
+        const int cut = a_lo < n_occ && n_occ < a_hi ? n_occ : a_hi;
+        for (int part = 0; part < 2; ++part) {
+          const int lo = part == 0 ? a_lo : cut, hi = part == 0 ? cut : a_hi;
+          for (int a0 = lo; a0 < hi; a0 += TA) {
+            const int ta = (hi - a0) < TA ? (hi - a0) : TA;
+            const int jstep = G > 1 ? n_occ : TJ;
+            for (int j0 = 0; j0 < n_occ; j0 += jstep) {
+              SegBatch b;
+              b.u_tgt = grid_ptr(p, true, kk, a0, n_occ, n_tgt);
+              b.ta = ta;
+              b.u_occ = grid_ptr(p, shared, q0, j0, n_occ, n_tgt);
+              b.G = G;
+              b.nj = (n_occ - j0) < jstep ? (n_occ - j0) : jstep;
+              b.w_occ = w_occ + (long long)q0 * n_occ + j0;
+              b.acc_a = acc_ptr(k, a0);
+              if (mirrored) {
+                b.acc_j = acc_ptr(q0, j0);
+                b.w_tgt = w_occ + (long long)k * n_occ + a0;
+              }
+              const int e = seg_batch(p, b, s);
+              if (e) return e;
+            }
           }
         }
+        q0 += G;
       }
-      if (upper) {
-        double2* acc_q = (double2*)p->acc.p + q * acc_k_elems;
-        for (int a0 = 0; a0 < n_occ; a0 += TA) {
-          const int ta = (n_occ - a0) < TA ? (n_occ - a0) : TA;
-          for (int j0 = 0; j0 < n_occ; j0 += TJ) {
-            const int tj = (n_occ - j0) < TJ ? (n_occ - j0) : TJ;
-            st = sym_batch(p, k, a0, ta, q, j0, tj, n_occ, n_tgt, w_occ,
-                           acc_k + (long long)a0 * n3(p), acc_q + (long long)j0 * n3(p), s);
-            if (st) return st;
+      return XX_OK;
+    };
+    if (!sym) {
+      if ((st = run_q(0, p->nk, 0, n_tgt, false))) return st;
+    } else {
+      // k = q: tiles I <= J of the occupied square (tiles J > I receive
+      // -(w_a/N_k) u_a conj(W_aj) through the role-swapped pass C), then the
+      // targets past the occupied set
+      if ((st = kernel_table_for(p, k, k, false, s))) return st;
+      for (int i0 = 0; i0 < n_occ; i0 += T) {
+        const int ti = (n_occ - i0) < T ? (n_occ - i0) : T;
+        for (int j0 = i0; j0 < n_occ; j0 += T) {
+          SegBatch b;
+          b.u_tgt = grid_ptr(p, true, k, i0, n_occ, n_tgt);
+          b.ta = ti;
+          b.u_occ = grid_ptr(p, true, k, j0, n_occ, n_tgt);
+          b.nj = (n_occ - j0) < T ? (n_occ - j0) : T;
+          b.w_occ = w_occ + (long long)k * n_occ + j0;
+          b.acc_a = acc_ptr(k, i0);
+          if (j0 > i0) {
+            b.acc_j = acc_ptr(k, j0);
+            b.w_tgt = w_occ + (long long)k * n_occ + i0;
           }
+          if ((st = seg_batch(p, b, s))) return st;
         }
       }
-      for (int a0 = a_first; a0 < n_tgt; a0 += TA) {
-        const int ta = (n_tgt - a0) < TA ? (n_tgt - a0) : TA;
-        for (int j0 = 0; j0 < n_occ; j0 += TJ) {
-          const int tj = (n_occ - j0) < TJ ? (n_occ - j0) : TJ;
-          PairArgs a = pair_args(p, ta, tj);
-          a.u_tgt = grid_ptr(p, true, kk, a0, n_occ, n_tgt);
-          a.u_occ = grid_ptr(p, shared, q, j0, n_occ, n_tgt);
-          a.acc = acc_k + (long long)a0 * n3(p);
-          a.w_occ = w_occ + (long long)q * n_occ + j0;
-          run_pass_a(p, a, s);
-          run_pass_b(p, a, s);
-          run_pass_c(p, a, s);
-          if ((st = launched(p, 3))) return st;
-        }
+      if ((st = run_q(k, k + 1, n_occ, n_tgt, false))) return st;
+      if (cross) {
+        // blocks q < k: their occupied squares ran with block (q, k)
+        if ((st = run_q(0, k, n_occ, n_tgt, false))) return st;
+        if ((st = run_q(k + 1, p->nk, 0, n_occ, true))) return st;
+        if ((st = run_q(k + 1, p->nk, n_occ, n_tgt, false))) return st;
+      } else {
+        if ((st = run_q(0, k, 0, n_tgt, false))) return st;
+        if ((st = run_q(k + 1, p->nk, 0, n_tgt, false))) return st;
       }
     }
-    // every contribution to the targets of k is in: blocks (k', k) with k' < k
-    // ran in earlier iterations
-    st = grid_to_sphere(p, k, acc_k, n_tgt, (double2*)vx_out + (long long)kk * n_tgt * p->npw_max, s);
+    // every contribution to the targets of k is in (blocks (k', k) with k' < k
+    // ran in earlier iterations); the split layout keeps them in two runs
+    double2* out = (double2*)vx_out + (long long)kk * n_tgt * p->npw_max;
+    if (split > 0) {
+      if ((st = grid_to_sphere(p, k, acc_ptr(k, 0), split, out, s))) return st;
+      st = grid_to_sphere(p, k, acc_ptr(k, split), n_tgt - split, out + (long long)split * p->npw_max, s);
+    } else {
+      st = grid_to_sphere(p, k, acc_ptr(k, 0), n_tgt, out, s);
+    }
     if (st) return st;
   }
   return XX_OK;
@@ -1142,8 +1237,10 @@ int run_vjp_occ(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, i
     cudaMemsetAsync(p->acc.p, 0, (size_t)n_occ * n3(p) * 16, s);
     for (int k = 0; k < p->nk; ++k) {
       if ((st = kernel_table_for(p, k, q, false, s))) return st;
-      for (int a0 = 0; a0 < n_tgt; a0 += TA) {
-        const int ta = (n_tgt - a0) < TA ? (n_tgt - a0) : TA;
+      // target batches never cross the split of the shared grids' layout
+      for (int a0 = 0, ta = 0; a0 < n_tgt; a0 += ta) {
+        const int a_end = p->split > 0 && a0 < p->split ? p->split : n_tgt;
+        ta = (a_end - a0) < TA ? (a_end - a0) : TA;
         for (int j0 = 0; j0 < n_occ; j0 += TJ) {
           const int tj = (n_occ - j0) < TJ ? (n_occ - j0) : TJ;
           const char* ut = grid_ptr(p, true, k, a0, n_occ, n_tgt);
@@ -1209,8 +1306,10 @@ int run_vjp_fused(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ,
     for (int q = 0; q < p->nk; ++q) {
       if ((st = kernel_table_for(p, k, q, false, s))) return st;
       double2* acc_q = (double2*)p->acc2.p + (long long)q * n_occ * nn;
-      for (int a0 = 0; a0 < n_tgt; a0 += TA) {
-        const int ta = (n_tgt - a0) < TA ? (n_tgt - a0) : TA;
+      // target batches never cross the split of the shared grids' layout
+      for (int a0 = 0, ta = 0; a0 < n_tgt; a0 += ta) {
+        const int a_end = p->split > 0 && a0 < p->split ? p->split : n_tgt;
+        ta = (a_end - a0) < TA ? (a_end - a0) : TA;
         for (int j0 = 0; j0 < n_occ; j0 += TJ) {
           const int tj = (n_occ - j0) < TJ ? (n_occ - j0) : TJ;
           const char* ut = grid_ptr(p, true, k, a0, n_occ, n_tgt);
@@ -1753,6 +1852,7 @@ int xx_plan_info(xx_plan p, xx_info* info) {
   info->peak_workspace_bytes = p->peak_bytes;
   info->kernel_launches = p->launches;
   info->pairs_transformed = p->pairs;
+  info->q_per_batch = p->g_last;
   return XX_OK;
 }
 

@@ -49,6 +49,12 @@ struct PairArgs {
   int stage_a;           // FP32 pass A: occupied planes by bulk copies into shared memory
   int test_wait_expiry;  // tests only: announce the first pass-B copy of each CTA 16
                          // bytes longer than it is, so its bounded wait runs out
+  // The occupied batch may span several q-points (their grids, occupations and
+  // accumulators laid out contiguously by the caller): column tj belongs to
+  // q-point segment tj / nj, whose kernel table starts vt_seg values after the
+  // previous one (one segment when nj >= TJ).
+  int nj;
+  long long vt_seg;
 };
 
 struct GridArgs {        // sphere <-> grid
@@ -540,7 +546,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_pass_b(PairArgs 
   const int P1 = p.P1, P2 = p.P2;
   const int zstride = P2 * p.LX;               // a pair's planes stay within 32-bit offsets
   C* row = reinterpret_cast<C*>(p.inter) + (long long)pair * N * zstride + kyb * p.LX;
-  const T* vt = reinterpret_cast<const T*>(p.vt) + kyb * P1;
+  const T* vt = reinterpret_cast<const T*>(p.vt) + (long long)((pair % p.TJ) / p.nj) * p.vt_seg + kyb * P1;
   pencil_forward<N, NT, T>(
       tw, sZ, P1, p.h3, [&](int z, int c) { return row[z * zstride + c]; },
       [&](int kzb, int c, C v) {
@@ -740,7 +746,8 @@ __global__ void __launch_bounds__(NT, 2) k_pass_b_tma(const __grid_constant__ CU
     // completes at once: makes the copied bytes visible to every thread
     mbar_wait(&bar[b], (it >> 1) & 1);
     const int kyb = item % P2, pair = item / P2;
-    const float* vt = reinterpret_cast<const float*>(p.vt) + kyb * P1;
+    const float* vt =
+        reinterpret_cast<const float*>(p.vt) + (long long)((pair % p.TJ) / p.nj) * p.vt_seg + kyb * P1;
     pencil_forward<N, NT, float>(
         tw, X, P1, p.h3, [&](int z, int c) { return X[z * LX + c]; },
         [&](int kzb, int c, C v) { sK[kzb * P1 + c] = vt[kzb * (P2 * P1) + c] * v; }, LX);

@@ -71,7 +71,8 @@ class xx_info(ctypes.Structure):
                 ("precision", ctypes.c_int), ("targets_per_batch", ctypes.c_int),
                 ("occupied_per_batch", ctypes.c_int), ("omega", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_size_t), ("peak_workspace_bytes", ctypes.c_size_t),
-                ("kernel_launches", ctypes.c_longlong), ("pairs_transformed", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong), ("pairs_transformed", ctypes.c_longlong),
+                ("q_per_batch", ctypes.c_int)]
 
 
 _lib = None

@@ -26,13 +26,17 @@ def transformed_set(nk, n_occ, n_tgt, T):
     return out
 
 
-@pytest.mark.parametrize("nk,n_occ,n_tgt,TA,TJ", [(1, 8, 8, 3, 3), (3, 5, 7, 2, 4),
-                                                   (4, 6, 6, 4, 4), (2, 9, 12, 5, 3),
-                                                   (8, 4, 6, 3, 3)])
-def test_schedule_transforms_every_pair_once(nk, n_occ, n_tgt, TA, TJ):
+@pytest.mark.parametrize("nk,n_occ,n_tgt,TA,TJ,G", [(1, 8, 8, 3, 3, 1), (3, 5, 7, 2, 4, 1),
+                                                     (4, 6, 6, 4, 4, 1), (2, 9, 12, 5, 3, 1),
+                                                     (8, 4, 6, 3, 3, 1), (8, 4, 6, 6, 4, 8),
+                                                     (5, 3, 5, 5, 3, 2), (7, 2, 2, 2, 2, 3)])
+def test_schedule_transforms_every_pair_once(nk, n_occ, n_tgt, TA, TJ, G):
+    """G > 1: several k-points' occupied sets share a batch (the same pairs, fewer
+    and wider launches)."""
     T = min(TA, TJ)
     tset = transformed_set(nk, n_occ, n_tgt, T)
-    sched = bench.batch_schedule(nk, n_occ, n_tgt, TA, TJ)
+    sched = bench.batch_schedule(nk, n_occ, n_tgt, TA, TJ, G)
+    assert all(tj <= max(TJ, G * n_occ) for _, _, tj in sched)
     assert sum(ta * tj for _, ta, tj in sched) == len(tset)
     # mirrored launches carry exactly the transformed pairs whose mirror is not
     # transformed itself (tiles I < J and blocks q > k)

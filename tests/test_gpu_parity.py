@@ -337,3 +337,31 @@ def test_grid_64_k_mesh(gpu, oracle_mod, prec, tol):
     assert gu.rel_max(got, ref) <= tol
     assert gu.hermitian_defect(wl.c_tgt, vx) <= max(tol, 1e-12)
     assert abs(e_im) <= max(tol, 1e-12) * abs(e)
+
+
+@pytest.mark.parametrize("shared", [True, False])
+def test_q_point_segments_match_single_q_batches(gpu, shared):
+    """Occupied sets of several k-points in one batch (default: 4 bands per k-point
+    and a batch 80 wide) against one k-point per batch (occupied width 4), FP64,
+    with the pair symmetry (shared grids, split layout) and without (separate
+    occupied array)."""
+    torch, xx = gpu
+    wl = rhombo24()
+    out = []
+    for batch in (None, (6, 4)):
+        plan = xx.Plan.from_workload(wl, precision=1)
+        if batch:
+            plan.set_batch(*batch)
+        if shared:
+            c = gu.dev(wl.c_tgt)
+            ex, vx = plan.energy(c, gu.dev(wl.w_occ), c, gu.dev(wl.w_tgt), shared=True)
+        else:
+            ex, vx = plan.energy(gu.dev(wl.c_occ), gu.dev(wl.w_occ), gu.dev(wl.c_tgt),
+                                 gu.dev(wl.w_tgt))
+        plan.sync(timeout_s=600.0)
+        info = plan.info()
+        out.append((vx.cpu().numpy(), float(ex[0].item()), info["q_per_batch"]))
+        plan.close()
+    assert out[0][2] == wl.nk and out[1][2] == 1
+    assert gu.rel_max(out[0][0], out[1][0]) <= 1e-12
+    assert abs(out[0][1] - out[1][1]) <= 1e-12 * abs(out[1][1])

@@ -127,3 +127,22 @@ def test_fused_vjp_falls_back_without_room(gpu):
     assert gu.rel_max(gt.cpu().numpy(), fused[0]) <= 1e-12
     assert gu.rel_max(go.cpu().numpy(), fused[1]) <= 1e-12
     plan.close()
+
+
+def test_vjp_with_shared_grids_matches_separate_arrays(gpu):
+    """Occupied bands passed as the leading target bands (ld_occ = n_tgt, the grids
+    then stored occupied-first) against a separate occupied array, FP64."""
+    torch, xx = gpu
+    wl = rhombo24()
+    rng = np.random.default_rng(5)
+    ybar = gu.dev(masked_random(rng, wl, wl.c_tgt.shape))
+    ref = gpu_vjp(xx, wl, ybar.cpu().numpy(), 1)
+    plan = xx.Plan.from_workload(wl, precision=1)
+    ct, wo = gu.dev(wl.c_tgt), gu.dev(wl.w_occ)
+    gt = torch.empty_like(ct)
+    go = torch.empty((wl.nk, wl.n_occ, wl.npw_max), dtype=ct.dtype, device=ct.device)
+    xx.xx_apply_vjp(plan.handle, ct, wl.n_tgt, wo, wl.n_occ, ct, wl.n_tgt, ybar, gt, go)
+    plan.sync(timeout_s=600.0)
+    assert gu.rel_max(gt.cpu().numpy(), ref[0]) <= 1e-12
+    assert gu.rel_max(go.cpu().numpy(), ref[1]) <= 1e-12
+    plan.close()
