@@ -245,6 +245,8 @@ def profile_case(args):
     __graft_entry__.build()
     from paper_1111_0716_gb300 import synth, xx
     wl = synth.beta_boron()
+    if args.profile_grid:
+        wl = wl.replace(grid=(args.profile_grid,) * 3)
     prec = xx.XX_FP64 if args.precision == "fp64" else xx.XX_FP32_MIXED
     if args.profile_shared:
         # the first two k-points with shared grids: k = q tiles, the pair-symmetric
@@ -403,6 +405,9 @@ def main():
     ap.add_argument("--profile-shared", action="store_true",
                     help="with --profile-case: xx_energy on the first two k-points with shared "
                          "grids (pair-symmetric batches, role-swapped pass C; about 25 GB)")
+    ap.add_argument("--profile-grid", type=int, default=0,
+                    help="with --profile-case: run the case on this FFT grid instead of 96^3 "
+                         "(any supported length >= 4 n_max + 1 = 57, e.g. 60)")
     ap.add_argument("--with-vjp", action="store_true",
                     help="also time the vector-Jacobian product (xx_apply_vjp, both orbital "
                          "sets) on 16 target bands of every k-point")
