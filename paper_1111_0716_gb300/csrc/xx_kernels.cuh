@@ -87,21 +87,24 @@ struct VtabArgs {
 // Shared-memory layout of a plane (N rows of LD complex values): between the
 // two steps of the x transform, row y holds slot k1*S + n2 (S >= B); the x
 // transform's output and the y transform's data sit at natural positions
-// (row y, column x or f_x).  S and LD are chosen per N so that the accesses of
-// every step, with the thread mappings below, hit distinct shared-memory banks
-// (all of them for N = 32 and 96; the replay ratio is at most 1.3 elsewhere).
+// (row y, column x or f_x).  S and LD are chosen per N (by counting, for the
+// thread mappings below, the bank-conflict wavefronts of 8-byte accesses in
+// half-warp phases over every S in [B, B + 16] and LD in [N, N + 40]) so that
+// the x-step accesses hit distinct banks for N = 32 and 96 and replay at most
+// 1.2x for N = 24, 60, 72 and 1.5x for N = 40, 48, 64, 80 (the y steps, lanes
+// over consecutive columns, never conflict).
 // FP32 planes use two buffers (the x-step exchange goes from one to the
 // other); FP64 planes use one buffer and hold a step's outputs in registers
 // across a barrier.
 
 template <int N> struct Lay;
-template <> struct Lay<24> { static constexpr int A = 8, B = 3, S = 3, LD = 28; };
+template <> struct Lay<24> { static constexpr int A = 8, B = 3, S = 4, LD = 35; };
 template <> struct Lay<32> { static constexpr int A = 8, B = 4, S = 5, LD = 44; };
 template <> struct Lay<40> { static constexpr int A = 8, B = 5, S = 5, LD = 44; };
 template <> struct Lay<48> { static constexpr int A = 8, B = 6, S = 7, LD = 60; };
-template <> struct Lay<60> { static constexpr int A = 6, B = 10, S = 11, LD = 67; };
+template <> struct Lay<60> { static constexpr int A = 6, B = 10, S = 15, LD = 90; };
 template <> struct Lay<64> { static constexpr int A = 8, B = 8, S = 9, LD = 76; };
-template <> struct Lay<72> { static constexpr int A = 8, B = 9, S = 9, LD = 76; };
+template <> struct Lay<72> { static constexpr int A = 8, B = 9, S = 12, LD = 105; };
 template <> struct Lay<80> { static constexpr int A = 8, B = 10, S = 11, LD = 92; };
 template <> struct Lay<96> { static constexpr int A = 8, B = 12, S = 13, LD = 108; };
 
