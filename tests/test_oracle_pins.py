@@ -155,6 +155,24 @@ def test_apply_equals_coefficient_space_double_convolution(oracle_mod, make):
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+def test_every_admissible_grid_gives_the_same_operator(oracle_mod):
+    """Under the no-wrap-around reading every grid with N >= 4 n_max + 1 gives the same
+    V_x c and E_x: the oracle on the tiny cell's 24^3 grid (n_max = 4, 4 n_max + 1 = 17)
+    against 18^3 and 20^3, and a grid below the bound (16^3) that does alias."""
+    wl = synth.tiny_cubic()
+    assert int(wl.n_max().max()) == 4
+    ref = oracle_mod.apply(wl)
+    e_ref, _ = oracle_mod.energy_from_vx(wl, ref)
+    for n in (18, 20):
+        other = wl.replace(grid=(n,) * 3)
+        vx = oracle_mod.apply(other)
+        e, _ = oracle_mod.energy_from_vx(other, vx)
+        assert np.abs(vx - ref).max() <= 1e-12 * np.abs(ref).max()
+        assert abs(e - e_ref) <= 1e-12 * abs(e_ref)
+    aliased = oracle_mod.apply(wl.replace(grid=(16,) * 3))
+    assert np.abs(aliased - ref).max() > 1e-6 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("make", [small_rhombo, synth.tiny_cubic])
 def test_hermiticity(oracle_mod, make):
     wl = make()
