@@ -8,8 +8,9 @@
 // multiplexing of the paper's innermost loop):
 //   pass A  one z-plane per CTA: codensity + forward x and y FFTs, output
 //           pruned to |f_x|,|f_y| <= 2 n_max (the codensity's exact support);
-//   pass B  one (pair, f_y) row per CTA: forward z FFT, multiply by the kernel
-//           table, inverse z FFT, in place;
+//   pass B  one (pair, f_y) row per CTA, or per item of a persistent CTA whose
+//           rows arrive by tensor copies: forward z FFT, multiply by the
+//           kernel table, inverse z FFT, in place;
 //   pass C  one z-plane per CTA: inverse y and x FFTs, multiply by u_qj and
 //           accumulate over the occupied batch in registers, then add into the
 //           FP64 accumulator of the target.
@@ -942,7 +943,8 @@ __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_c(PairArgs p) {
 // or 1 when w_tgt is null), then adds coef * w_occ[j] (or coef) times the plane
 // into the FP64 accumulator of j.  Uses: the vector-Jacobian product with
 // respect to the occupied orbitals (f = cotangent or target grids, weight
-// w_j), and the k = q pair symmetry W_ja = conj(W_aj) (f_a = u_a, weight w_a).
+// w_j), and the pair symmetry W_qj,ka = conj(W_ka,qj) (f_a = u_a, weight w_a)
+// on k = q tiles and k != q blocks.
 template <int N, typename T>
 __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_ct(PairArgs p) {
   using C = cplx<T>;
