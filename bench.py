@@ -394,8 +394,9 @@ def main():
                     help="skip the smallest-exact-grid leg")
     ap.add_argument("--no-alpha", action="store_true", help="skip the alpha-boron-sized leg")
     ap.add_argument("--profile-case", action="store_true",
-                    help="run one small slice of the workload (k=0, 16 targets, 32 occupied "
-                         "bands, all q) once and exit: the case ncu captures")
+                    help="run one slice of the workload (k=0, 64 targets x 80 occupied bands, "
+                         "all q: one launch per pass in the benchmark's batch shape) once and "
+                         "exit: the case ncu captures")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="precision of --profile-case")
     ap.add_argument("--profile-small", action="store_true",
