@@ -41,9 +41,12 @@ def _build_oracle(force: bool) -> str:
 
 
 def lib():
+    """The loaded oracle library.  XX_ORACLE_LIB names another compiled copy of
+    ``xx_oracle.c`` to load instead (the tests use it to check that the pins
+    reject deliberately broken copies); otherwise the source is built here."""
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build_oracle())
+        _lib = ctypes.CDLL(os.environ.get("XX_ORACLE_LIB") or build_oracle())
         P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
         _lib.oracle_fft3d.argtypes = [P, I, I, I, I]
         _lib.oracle_cell_volume.argtypes = [P]
