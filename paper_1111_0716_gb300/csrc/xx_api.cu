@@ -661,14 +661,16 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// Pass B of one batch.  FP32 takes the tensor-copy staged kernel: the
-// intermediates viewed as floats [N * pairs][P2][2 LX], one box of 2 LX x 1 x N
-// (a row's N z-planes) per item; a row is 8 LX bytes (a multiple of 16, LX even).
+// Pass B of one batch.  In FP32, when the kept f_x are at most 3/4 of a row (or
+// when forced), it takes the tensor-copy staged kernel: the intermediates viewed
+// as floats [N * pairs][P2][2 LX], one box of 2 LX x 1 x N (a row's N z-planes)
+// per item; a row is 8 LX bytes (a multiple of 16, LX even).
 void run_pass_b(xx_plan p, const PairArgs& a, cudaStream_t s) {
   const int e = prof_begin(p, s);
   bool done = false;
   // measured on GB300 (beta cell, 64 targets x 160 occupied x 8 q): P1 = 57 of N = 96,
-  // tensor-copy kernel 4.5 % faster than the row kernel; P1 = 57 of N = 60, 14 % slower
+  // tensor-copy kernel 6.7 % faster than the row kernel (243.9 vs 261.3 ms); P1 = 57
+  // of N = 60, 14 % slower
   const bool want = p->tma_pass_b == 2 || (p->tma_pass_b == 1 && 4 * a.P1 <= 3 * p->N);
   PFN_cuTensorMapEncodeTiled_v12000 enc = p->prec == XX_FP32_MIXED && want ? tensor_map_encoder() : nullptr;
   if (enc && 2 * a.LX <= 256 && p->N <= 256) {
