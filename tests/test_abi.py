@@ -125,3 +125,9 @@ def test_exact_grid_is_the_smallest_admissible_supported_length(lib):
         assert wl.grid[0] >= 4 * nm.max() + 1
     assert _status(lambda: lib.xx_exact_grid((24, 0, 0))) == -2
     assert _status(lambda: lib.xx_exact_grid((-1, 0, 0))) == -1
+
+
+def test_binding_has_a_function_for_every_entry_point(lib):
+    """The Python binding is thin: one function per C entry point, same name."""
+    for n in declared_symbols():
+        assert callable(getattr(lib, n, None)), n
