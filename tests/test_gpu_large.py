@@ -61,10 +61,15 @@ def test_beta_boron_96_gamma222(gpu, oracle_mod):
     vx, (e, e_im), info = gu.run(wl, 0)
     assert abs(e_im) <= gu.FP32_TOL * abs(e)
     assert gu.hermitian_defect(wl.c_tgt, vx) <= gu.FP32_TOL
-    # a target at a zone-boundary k-point in the fractionally occupied range
-    k, a = wl.nk - 1, 155
-    ref = oracle_mod.apply(wl, sel=[(k, a)])[0]
-    assert gu.rel_max(vx[k, a], ref) <= gu.FP32_TOL
+    # sampled targets: the first band at Gamma (a k = q diagonal tile), a target past
+    # the occupied set at an inner k-point (every occupied band of every q, no pair
+    # symmetry), and a fractionally occupied band at the zone-boundary k-point
+    sel = [(0, 0), (3, wl.n_tgt - 1), (wl.nk - 1, 155)]
+    refs = oracle_mod.apply(wl, sel=sel)
+    for (kk, aa), r in zip(sel, refs):
+        assert gu.rel_max(vx[kk, aa], r) <= gu.FP32_TOL, (kk, aa)
+    k, a = sel[-1]
+    ref = refs[-1]
     d_gpu = np.vdot(wl.c_tgt[k, a], vx[k, a]).real
     d_ref = np.vdot(wl.c_tgt[k, a], ref).real
     assert abs(d_gpu - d_ref) <= gu.FP32_TOL * abs(d_ref)
