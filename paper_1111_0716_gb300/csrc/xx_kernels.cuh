@@ -88,12 +88,12 @@ struct VtabArgs {
 // Shared-memory layout of a plane (N rows of LD complex values): between the
 // two steps of the x transform, row y holds slot k1*S + n2 (S >= B); the x
 // transform's output and the y transform's data sit at natural positions
-// (row y, column x or f_x).  S and LD are chosen per N (by counting, for the
-// thread mappings below, the bank-conflict wavefronts of 8-byte accesses in
-// half-warp phases over every S in [B, B + 16] and LD in [N, N + 40]) so that
-// the x-step accesses hit distinct banks for N = 32 and 96 and replay at most
-// 1.2x for N = 24, 60, 72 and 1.5x for N = 40, 48, 64, 80 (the y steps, lanes
-// over consecutive columns, never conflict).
+// (row y, column x or f_x).  S and LD are chosen per N by csrc/bank_layout.py,
+// which counts the wavefronts of 8-byte accesses in half-warp phases over every
+// S in [B, B + 16] and LD in [N, N + 40]: the x steps replay 1.0x at N = 32, 96,
+// at most 1.2x at N = 24, 60, 72 and 1.5x at N = 40, 48, 64, 80.  The y steps
+// (lanes over kept columns) are conflict-free when 16 divides N; otherwise the
+// wrap from column N - 1 to column 0 replays up to 2x in one half-warp.
 // FP32 planes use two buffers (the x-step exchange goes from one to the
 // other); FP64 planes use one buffer and hold a step's outputs in registers
 // across a barrier.
