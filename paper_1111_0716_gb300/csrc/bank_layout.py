@@ -158,16 +158,26 @@ def y_cost(N, h):
     return cost, ideal
 
 
-def staged_read_cost(N, A, B):
+def staged_read_cost(N, A, B, pitch=None):
     """(wavefronts, ideal) of the staged pass A's first x step reading the
-    bulk-copied occupied plane (row pitch N): lane item it reads row it / B,
-    column B*n1 + it % B."""
+    bulk-copied occupied plane (row pitch N as committed, or `pitch`): lane item
+    it reads row it / B, column B*n1 + it % B."""
+    pitch = N if pitch is None else pitch
     out = []
     for its in _warps(nt_staged(N, A, B), N * B):
         for n1 in range(A):
-            out.append(phase_cost([None if it is None else (it // B) * N + B * n1 + it % B
+            out.append(phase_cost([None if it is None else (it // B) * pitch + B * n1 + it % B
                                    for it in its]))
     return _sum(out)
+
+
+def conflict_free_pitch(N, B):
+    """Smallest row pitch >= N equal to B modulo 16: lane item it then reads element
+    it + B*n1 (mod 16), so a half-warp hits 16 distinct bank pairs."""
+    pitch = N
+    while pitch % 16 != B % 16:
+        pitch += 1
+    return pitch
 
 
 def search(N, A, B):

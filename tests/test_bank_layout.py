@@ -58,3 +58,14 @@ def test_y_steps_conflict_only_at_the_column_wrap(N):
             assert c == i, h
         else:
             assert c <= 2 * i, h
+
+
+@pytest.mark.parametrize("N", sorted(LAY))
+def test_staged_reads_conflict_free_at_a_pitch_of_b_mod_16(N):
+    """The staged plane's reads replay at pitch N; a pitch equal to B modulo 16 removes
+    every conflict (the layout a padded staging would use)."""
+    A, B, S, LD = LAY[N]
+    c, i = bl.staged_read_cost(N, A, B)
+    assert c >= i
+    c, i = bl.staged_read_cost(N, A, B, bl.conflict_free_pitch(N, B))
+    assert c == i
