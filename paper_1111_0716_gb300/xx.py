@@ -132,14 +132,57 @@ def _stream_ptr(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _dptr(t):
+_DTYPES = {"c128": "torch.complex128", "f64": "torch.float64", "i32": "torch.int32"}
+
+
+def _dptr(t, name="tensor", kind=None, need=0, npw=None):
+    """Device pointer of t (None passes as NULL).  The C entry points take plain
+    pointers and cannot see sizes or types, so the binding checks them here: a
+    contiguous CUDA tensor of the element type `kind` holding at least `need`
+    elements; orbital arrays (npw given) must have the plan's padded basis
+    length as their last dimension."""
     if t is None:
         return None
     if not t.is_cuda:
-        raise ValueError("expected a CUDA tensor")
+        raise ValueError("%s: expected a CUDA tensor" % name)
     if not t.is_contiguous():
-        raise ValueError("expected a contiguous tensor")
+        raise ValueError("%s: expected a contiguous tensor" % name)
+    if kind is not None and str(t.dtype) != _DTYPES[kind]:
+        raise ValueError("%s: expected %s, got %s" % (name, _DTYPES[kind], t.dtype))
+    if t.numel() < need:
+        raise ValueError("%s: holds %d elements, the call uses %d" % (name, t.numel(), need))
+    if npw is not None and t.dim() >= 2 and t.shape[-1] != npw:
+        raise ValueError("%s: last dimension %d, the plan's padded basis has %d"
+                         % (name, t.shape[-1], npw))
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _dims(plan):
+    """(nk, npw_max) of a plan, or None for a null or invalid handle (the C call
+    then reports it)."""
+    if plan is None or (isinstance(plan, ctypes.c_void_p) and not plan.value):
+        return None
+    info = xx_info()
+    if load().xx_plan_info(plan, ctypes.byref(info)) != XX_OK:
+        return None
+    return int(info.nk), int(info.npw_max)
+
+
+def _orbitals(plan, nk_used=None):
+    """Helpers for one call: c(t, name, nb) checks a complex128 [nk][nb][npw_max]
+    array, w(t, name, nb) a float64 [nk][nb] one, over nk_used k-points (all of
+    the plan's by default); both pass everything when the plan is invalid."""
+    d = _dims(plan)
+    if d is None:
+        return (lambda t, name, nb: _dptr(t, name)), (lambda t, name, nb: _dptr(t, name))
+    nk, npw = d
+    n = nk if nk_used is None else max(0, int(nk_used))
+    return (lambda t, name, nb: _dptr(t, name, "c128", n * max(0, int(nb)) * npw, npw),
+            lambda t, name, nb: _dptr(t, name, "f64", n * max(0, int(nb))))
+
+
+def _ld(ld_occ, n_occ):
+    return int(ld_occ) if int(ld_occ) > 0 else int(n_occ)
 
 
 # ------------------------------------------------------- C entry points --
@@ -168,61 +211,89 @@ def xx_destroy(plan):
 
 
 def xx_apply(plan, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, vx_out, stream=None):
-    _check(load().xx_apply(plan, _dptr(c_occ), int(ld_occ), _dptr(w_occ), int(n_occ),
-                           _dptr(c_tgt), int(n_tgt), _dptr(vx_out), _stream_ptr(stream)),
+    c, w = _orbitals(plan)
+    _check(load().xx_apply(plan, c(c_occ, "c_occ", _ld(ld_occ, n_occ)), int(ld_occ),
+                           w(w_occ, "w_occ", n_occ), int(n_occ), c(c_tgt, "c_tgt", n_tgt),
+                           int(n_tgt), c(vx_out, "vx_out", n_tgt), _stream_ptr(stream)),
            "xx_apply")
 
 
 def xx_apply_range(plan, k_first, k_count, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, vx_out,
                    stream=None):
-    _check(load().xx_apply_range(plan, int(k_first), int(k_count), _dptr(c_occ), int(ld_occ),
-                                 _dptr(w_occ), int(n_occ), _dptr(c_tgt), int(n_tgt),
-                                 _dptr(vx_out), _stream_ptr(stream)), "xx_apply_range")
+    c, w = _orbitals(plan)
+    cr, _ = _orbitals(plan, k_count)
+    _check(load().xx_apply_range(plan, int(k_first), int(k_count),
+                                 c(c_occ, "c_occ", _ld(ld_occ, n_occ)), int(ld_occ),
+                                 w(w_occ, "w_occ", n_occ), int(n_occ), cr(c_tgt, "c_tgt", n_tgt),
+                                 int(n_tgt), cr(vx_out, "vx_out", n_tgt), _stream_ptr(stream)),
+           "xx_apply_range")
 
 
 def xx_energy_range(plan, k_first, k_count, c_occ, ld_occ, w_occ, n_occ, c_tgt, w_tgt, n_tgt,
                     vx_out, ex_out, stream=None):
-    _check(load().xx_energy_range(plan, int(k_first), int(k_count), _dptr(c_occ), int(ld_occ),
-                                  _dptr(w_occ), int(n_occ), _dptr(c_tgt), _dptr(w_tgt),
-                                  int(n_tgt), _dptr(vx_out), _dptr(ex_out), _stream_ptr(stream)),
-           "xx_energy_range")
+    c, w = _orbitals(plan)
+    cr, wr = _orbitals(plan, k_count)
+    _check(load().xx_energy_range(plan, int(k_first), int(k_count),
+                                  c(c_occ, "c_occ", _ld(ld_occ, n_occ)), int(ld_occ),
+                                  w(w_occ, "w_occ", n_occ), int(n_occ), cr(c_tgt, "c_tgt", n_tgt),
+                                  wr(w_tgt, "w_tgt", n_tgt), int(n_tgt),
+                                  cr(vx_out, "vx_out", n_tgt), _dptr(ex_out, "ex_out", "f64", 2),
+                                  _stream_ptr(stream)), "xx_energy_range")
 
 
 def xx_energy_from_vx_range(plan, k_first, k_count, c_tgt, w_tgt, n_tgt, vx, ex_out, stream=None):
-    _check(load().xx_energy_from_vx_range(plan, int(k_first), int(k_count), _dptr(c_tgt),
-                                          _dptr(w_tgt), int(n_tgt), _dptr(vx), _dptr(ex_out),
-                                          _stream_ptr(stream)), "xx_energy_from_vx_range")
+    cr, wr = _orbitals(plan, k_count)
+    _check(load().xx_energy_from_vx_range(plan, int(k_first), int(k_count),
+                                          cr(c_tgt, "c_tgt", n_tgt), wr(w_tgt, "w_tgt", n_tgt),
+                                          int(n_tgt), cr(vx, "vx", n_tgt),
+                                          _dptr(ex_out, "ex_out", "f64", 2), _stream_ptr(stream)),
+           "xx_energy_from_vx_range")
 
 
 def xx_energy(plan, c_occ, ld_occ, w_occ, n_occ, c_tgt, w_tgt, n_tgt, vx_out, ex_out, stream=None):
-    _check(load().xx_energy(plan, _dptr(c_occ), int(ld_occ), _dptr(w_occ), int(n_occ),
-                            _dptr(c_tgt), _dptr(w_tgt), int(n_tgt), _dptr(vx_out), _dptr(ex_out),
-                            _stream_ptr(stream)), "xx_energy")
+    c, w = _orbitals(plan)
+    _check(load().xx_energy(plan, c(c_occ, "c_occ", _ld(ld_occ, n_occ)), int(ld_occ),
+                            w(w_occ, "w_occ", n_occ), int(n_occ), c(c_tgt, "c_tgt", n_tgt),
+                            w(w_tgt, "w_tgt", n_tgt), int(n_tgt), c(vx_out, "vx_out", n_tgt),
+                            _dptr(ex_out, "ex_out", "f64", 2), _stream_ptr(stream)), "xx_energy")
 
 
 def xx_energy_from_vx_noalloc(nk, n_tgt, npw_max, npw, c_tgt, w_tgt, vx, ex_out, stream=None):
     """E_x reduction without a plan or any device allocation (fixed device scratch)."""
-    _check(load().xx_energy_from_vx_noalloc(int(nk), int(n_tgt), int(npw_max), _dptr(npw),
-                                            _dptr(c_tgt), _dptr(w_tgt), _dptr(vx), _dptr(ex_out),
-                                            _stream_ptr(stream)), "xx_energy_from_vx_noalloc")
+    nk, n_tgt, npw_max = int(nk), int(n_tgt), int(npw_max)
+    rows = max(0, nk) * max(0, n_tgt)
+    _check(load().xx_energy_from_vx_noalloc(
+        nk, n_tgt, npw_max, _dptr(npw, "npw", "i32", max(0, nk)),
+        _dptr(c_tgt, "c_tgt", "c128", rows * max(0, npw_max)),
+        _dptr(w_tgt, "w_tgt", "f64", rows), _dptr(vx, "vx", "c128", rows * max(0, npw_max)),
+        _dptr(ex_out, "ex_out", "f64", 2), _stream_ptr(stream)), "xx_energy_from_vx_noalloc")
 
 
 def xx_energy_from_vx(plan, c_tgt, w_tgt, n_tgt, vx, ex_out, stream=None):
-    _check(load().xx_energy_from_vx(plan, _dptr(c_tgt), _dptr(w_tgt), int(n_tgt), _dptr(vx),
-                                    _dptr(ex_out), _stream_ptr(stream)), "xx_energy_from_vx")
+    c, w = _orbitals(plan)
+    _check(load().xx_energy_from_vx(plan, c(c_tgt, "c_tgt", n_tgt), w(w_tgt, "w_tgt", n_tgt),
+                                    int(n_tgt), c(vx, "vx", n_tgt),
+                                    _dptr(ex_out, "ex_out", "f64", 2), _stream_ptr(stream)),
+           "xx_energy_from_vx")
 
 
 def xx_apply_backward(plan, c, w, n_b, vx, grad_ex, dc_out, dmu_out, stream=None):
-    _check(load().xx_apply_backward(plan, _dptr(c), _dptr(w), int(n_b), _dptr(vx),
-                                    float(grad_ex), _dptr(dc_out), _dptr(dmu_out),
-                                    _stream_ptr(stream)), "xx_apply_backward")
+    co, wo = _orbitals(plan)
+    _check(load().xx_apply_backward(plan, co(c, "c", n_b), wo(w, "w", n_b), int(n_b),
+                                    co(vx, "vx", n_b), float(grad_ex), co(dc_out, "dc_out", n_b),
+                                    _dptr(dmu_out, "dmu_out", "f64", 1), _stream_ptr(stream)),
+           "xx_apply_backward")
 
 
 def xx_apply_vjp(plan, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, ybar, grad_tgt_out,
                  grad_occ_out, stream=None):
-    _check(load().xx_apply_vjp(plan, _dptr(c_occ), int(ld_occ), _dptr(w_occ), int(n_occ),
-                               _dptr(c_tgt), int(n_tgt), _dptr(ybar), _dptr(grad_tgt_out),
-                               _dptr(grad_occ_out), _stream_ptr(stream)), "xx_apply_vjp")
+    c, w = _orbitals(plan)
+    _check(load().xx_apply_vjp(plan, c(c_occ, "c_occ", _ld(ld_occ, n_occ)), int(ld_occ),
+                               w(w_occ, "w_occ", n_occ), int(n_occ), c(c_tgt, "c_tgt", n_tgt),
+                               int(n_tgt), c(ybar, "ybar", n_tgt),
+                               c(grad_tgt_out, "grad_tgt_out", n_tgt),
+                               c(grad_occ_out, "grad_occ_out", n_occ), _stream_ptr(stream)),
+           "xx_apply_vjp")
 
 
 def xx_run_many(jobs, stream=None):
@@ -233,16 +304,18 @@ def xx_run_many(jobs, stream=None):
     for i, j in enumerate(jobs):
         n_occ = j["w_occ"].shape[1]
         ld = j.get("ld_occ", j["c_occ"].shape[1])
+        n_tgt = j["c_tgt"].shape[1]
+        c, w = _orbitals(j["plan"].handle)
         arr[i].plan = j["plan"].handle
-        arr[i].c_occ = _dptr(j["c_occ"])
+        arr[i].c_occ = c(j["c_occ"], "c_occ", _ld(ld, n_occ))
         arr[i].ld_occ = int(ld)
-        arr[i].w_occ = _dptr(j["w_occ"])
+        arr[i].w_occ = w(j["w_occ"], "w_occ", n_occ)
         arr[i].n_occ = int(n_occ)
-        arr[i].c_tgt = _dptr(j["c_tgt"])
-        arr[i].w_tgt = _dptr(j.get("w_tgt"))
-        arr[i].n_tgt = int(j["c_tgt"].shape[1])
-        arr[i].vx_out = _dptr(j["vx_out"])
-        arr[i].ex_out = _dptr(j.get("ex_out"))
+        arr[i].c_tgt = c(j["c_tgt"], "c_tgt", n_tgt)
+        arr[i].w_tgt = w(j.get("w_tgt"), "w_tgt", n_tgt)
+        arr[i].n_tgt = int(n_tgt)
+        arr[i].vx_out = c(j["vx_out"], "vx_out", n_tgt)
+        arr[i].ex_out = _dptr(j.get("ex_out"), "ex_out", "f64", 2)
     _check(load().xx_run_many(len(jobs), arr, _stream_ptr(stream)), "xx_run_many")
 
 
@@ -251,8 +324,11 @@ def xx_sync(plan, stream=None, timeout_s: float = 0.0):
 
 
 def xx_strain_derivative(plan, c, w, n_b, dex_deps, ex_out=None, stream=None):
-    _check(load().xx_strain_derivative(plan, _dptr(c), _dptr(w), int(n_b), _dptr(dex_deps),
-                                       _dptr(ex_out), _stream_ptr(stream)), "xx_strain_derivative")
+    co, wo = _orbitals(plan)
+    _check(load().xx_strain_derivative(plan, co(c, "c", n_b), wo(w, "w", n_b), int(n_b),
+                                       _dptr(dex_deps, "dex_deps", "f64", 9),
+                                       _dptr(ex_out, "ex_out", "f64", 1), _stream_ptr(stream)),
+           "xx_strain_derivative")
 
 
 def xx_set_option(plan, option: int, value: int):
