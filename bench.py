@@ -14,7 +14,10 @@ Printed as one JSON line (rank 0):
              launch duration (events on its stream during the timed steps),
              against the measured HBM copy bandwidth
   cpu_baseline  the FP64 CPU oracle, as it stands, on a bounded sample
-  fp64_slice    the all-FP64 GPU path on a slice of the same workload
+  fp64       the all-FP64 GPU path on one target k-point at the production batch
+             shape, with its ALU fraction against the measured FP64 FMA rate
+  parity     the CUDA path (both precisions) against the oracle on the
+             cpu_baseline sample
   real_gamma    the real-orbital Gamma path against the general path on the same
                 cell at the Gamma point only (real orbitals, 30,720 pairs)
   exact_grid    the same workload with the plan on the smallest grid on which the
@@ -196,15 +199,32 @@ def pass_bytes_per_step(wl, schedule, elem=8):
     return {"pass_a": a, "pass_b": b, "pass_c": c}
 
 
-def run_oracle_sample(wl, n_occ_sample):
+def run_oracle_sample(wl, n_occ_sample, want_vx=False):
     """The FP64 oracle on target (k=0, a=0), all q, the first n_occ_sample occupied bands."""
     from oracle import oracle
     t0 = time.perf_counter()
-    oracle.apply(wl, sel=[(0, 0)], c_occ=wl.c_occ[:, :n_occ_sample],
-                 w_occ=wl.w_occ[:, :n_occ_sample])
+    vx = oracle.apply(wl, sel=[(0, 0)], c_occ=wl.c_occ[:, :n_occ_sample],
+                      w_occ=wl.w_occ[:, :n_occ_sample])
     dt = time.perf_counter() - t0
     pairs = wl.nk * n_occ_sample
+    if want_vx:
+        return pairs / dt, dt, pairs, oracle.num_threads(), vx
     return pairs / dt, dt, pairs, oracle.num_threads()
+
+
+# Nominal flops of one transformed band pair on an N^3 grid pruned to P = 4 n_max + 1
+# frequencies per axis: the line transforms the passes run (pass A: N^2 x-lines and
+# N P y-lines; pass B: P^2 forward and P^2 inverse z-lines; pass C: N P y-lines and
+# N^2 x-lines) at the usual 5 L log2 L flops per length-L transform, plus the
+# pointwise work (codensity 6, kernel multiply 2 per kept frequency, u_j multiply and
+# weighted accumulate 8 flops per point).
+def flops_per_pair(N, P):
+    import math
+    line = 5.0 * N * math.log2(N)
+    a = N * (N + P) * line + 6.0 * N ** 3
+    b = 2.0 * P * P * line + 2.0 * P ** 3
+    c = N * (N + P) * line + 8.0 * N ** 3
+    return {"pass_a": a, "pass_b": b, "pass_c": c}
 
 
 def reference_arm(args, rank, world):
@@ -538,13 +558,28 @@ def main():
     bytes_per_launch = model[dom] * args.steps / max(n_l, 1)
     achieved = bytes_per_launch / mean_s / 1e9 if mean_s > 0 else 0.0
     path_bytes = sum(model.values()) * args.steps
+    traffic = recorded_traffic(dom, [TA, TJ])
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "peak_kind": peak_kind,
-                "traffic": recorded_traffic(dom, [TA, TJ]),
+                "frac": achieved / hbm, "frac_kind": "model bytes (algorithmic) / time",
+                "peak_kind": peak_kind, "traffic": traffic,
+                "dram_frac": (traffic / mean_s / 1e9 / hbm) if traffic and mean_s > 0 else None,
                 "bytes_per_launch": bytes_per_launch, "mean_launch_ms": mean_s * 1e3,
                 "launches": n_l,
                 "path": {"achieved": path_bytes / t / 1e9, "frac": path_bytes / t / 1e9 / hbm,
                          "bytes_per_logical_pair_per_point": path_bytes / args.steps / pairs / (96 ** 3)}}
+    # ALU view of the same kernel: nominal flops of its transforms and pointwise work
+    # over its event-timed launches, against the measured FP32 FMA rate
+    P1 = 4 * int(wl.n_max().max()) + 1
+    fpp = flops_per_pair(96, P1)
+    kflops = 0.0
+    for kind, ta, tj in sched:
+        kflops += fpp[dom] * ta * tj * (2 if (dom == "pass_c" and kind == "mirrored") else 1)
+    fp32_peak = xx.xx_measure_fma_rate(xx.XX_FP32_MIXED) if rank == 0 else None
+    if fp32_peak:
+        alu = kflops * args.steps / max(n_l, 1) / mean_s / 1e12 if mean_s > 0 else 0.0
+        roofline["alu"] = {"achieved": alu, "peak": fp32_peak, "unit": "TFLOP/s", "frac": alu / fp32_peak,
+                           "peak_kind": "measured FP32 FMA rate (xx_measure_fma_rate)",
+                           "flops_per_pair": fpp[dom]}
     shares = {k: v[0] for k, v in prof.items() if v[1]}
     tot = sum(shares.values()) or 1.0
     kernel_share = {k: round(v / tot, 4) for k, v in shares.items()}
@@ -569,9 +604,10 @@ def main():
         line["clocks"] = clk
 
     if rank == 0 and not args.no_fp64:
-        # all-FP64 GPU path on a slice: target k=0, 4 target bands, 16 occupied, all q
+        # all-FP64 GPU path on one target k-point at the production batch shape: target
+        # k=0, 64 target bands x all 160 occupied bands x 8 q (81,920 pairs)
         p64 = xx.Plan.from_workload(wl, precision=xx.XX_FP64)
-        nt, no = 4, 16
+        nt, no = 64, wl.n_occ
         ct = torch.from_numpy(wl.c_tgt[:1, :nt].copy()).cuda()
         co = torch.from_numpy(wl.c_occ[:, :no].copy()).cuda()
         wo = torch.from_numpy(wl.w_occ[:, :no].copy()).cuda()
@@ -585,6 +621,7 @@ def main():
         g1.record(stream)
         torch.cuda.synchronize()
         t64 = g0.elapsed_time(g1) / 1e3
+        info64 = p64.info()
         p_slice = nt * wl.nk * no
         # same slice in mixed precision for the like-for-like ratio
         p32 = xx.Plan.from_workload(wl, precision=xx.XX_FP32_MIXED)
@@ -596,10 +633,18 @@ def main():
         g1.record(stream)
         torch.cuda.synchronize()
         t32 = g0.elapsed_time(g1) / 1e3
-        line["fp64_slice"] = {"value": p_slice / t64, "unit": UNIT,
-                              "fp32_mixed_same_slice": p_slice / t32,
-                              "sample": "target k=0, %d target x %d occupied bands x 8 q = %d pairs"
-                              % (nt, no, p_slice)}
+        fp64_peak = xx.xx_measure_fma_rate(xx.XX_FP64)
+        fl = sum(fpp.values()) * p_slice
+        line["fp64"] = {"value": p_slice / t64, "unit": UNIT,
+                        "fp32_mixed_same_slice": p_slice / t32,
+                        "batch": [info64["targets_per_batch"], info64["occupied_per_batch"]],
+                        "alu": {"achieved": fl / t64 / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                                "frac": fl / t64 / 1e12 / fp64_peak,
+                                "peak_kind": "measured FP64 FMA rate (xx_measure_fma_rate)",
+                                "flops_per_pair": sum(fpp.values())},
+                        "fp32_mixed_alu_frac_same_slice": fl / t32 / 1e12 / fp32_peak if fp32_peak else None,
+                        "sample": "target k=0, %d target x %d occupied bands x 8 q = %d pairs, "
+                                  "no pair symmetry (separate occupied array)" % (nt, no, p_slice)}
         p64.close()
         p32.close()
 
@@ -641,10 +686,26 @@ def main():
                                  "returns dL/dc_tgt* and dL/dc_occ*" % (nt, p_slice)}
 
     if rank == 0 and world == 1 and not args.no_baseline:
-        r, dt, p_s, cores = run_oracle_sample(wl, args.oracle_occ)
+        r, dt, p_s, cores, vx_o = run_oracle_sample(wl, args.oracle_occ, want_vx=True)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": "target (k=0, a=0) x 8 q x %d occupied = %d pairs, %.1f s"
                                 % (args.oracle_occ, p_s, dt)}
+        # parity on the same sample: the CUDA path in both precisions against the oracle
+        no = args.oracle_occ
+        co = torch.from_numpy(wl.c_occ[:, :no].copy()).cuda()
+        wo = torch.from_numpy(wl.w_occ[:, :no].copy()).cuda()
+        ct = torch.from_numpy(wl.c_tgt[:1, :1].copy()).cuda()
+        ref = np.asarray(vx_o).reshape(-1)
+        c0 = wl.c_tgt[0, 0]
+        d_ref = np.vdot(c0, ref).real
+        par = {"sample": "target (k=0, a=0) x 8 q x %d occupied (the cpu_baseline sample)" % no}
+        for name, prec in (("fp32_mixed", xx.XX_FP32_MIXED), ("fp64", xx.XX_FP64)):
+            pp = xx.Plan.from_workload(wl, precision=prec)
+            got = pp.apply_range(0, 1, co, wo, ct).cpu().numpy().reshape(-1)
+            pp.close()
+            par[name] = {"max_dVx_over_max_Vx": float(np.abs(got - ref).max() / np.abs(ref).max()),
+                         "c_Vx_c_rel": float(abs(np.vdot(c0, got).real - d_ref) / abs(d_ref))}
+        line["parity"] = par
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -393,14 +393,20 @@ int xx_exact_grid(const int *n_max, int *n_out);
  * fixed-order FP64 reduction as xx_energy_from_vx, needs no plan, and calls no
  * cudaMalloc, cudaFree or allocating library routine.
  *   nk, n_tgt, npw_max: sizes of c_tgt and vx ([nk][n_tgt][npw_max] complex128,
- *       device); npw: device int [nk] basis sizes; w_tgt: device double
- *       [nk][n_tgt]; ex_out: device double[2] = {Re E_x, Im E_x}.
+ *       device); npw: device int [nk] basis sizes, each required to satisfy
+ *       1 <= npw[k] <= npw_max (the kernel clamps a value outside [0, npw_max]
+ *       to that range, so a bad size never reads past a row, but the result is
+ *       then that of the clamped size); w_tgt: device double [nk][n_tgt];
+ *       ex_out: device double[2] = {Re E_x, Im E_x}.
  * Its per-target partial sums live in one fixed device array of
  * XX_NOALLOC_MAX_ROWS complex128 entries (256 KiB) that every GPU loading the
  * library holds until the process exits; nk * n_tgt above that limit returns
  * XX_ERR_SIZE_LIMIT.  The first call on a device looks up the array's device
  * address (with that device current), so make that first call before any
- * stream capture.  All calls on a device share the array: calls whose work
+ * stream capture.  The address is kept for the life of the process: after
+ * cudaDeviceReset (or anything else that destroys the device's primary
+ * context) the module may load elsewhere, so a reset after the first call on a
+ * device is not supported.  All calls on a device share the array: calls whose work
  * overlaps on the GPU (different streams, concurrent threads) race and must be
  * serialised by the caller.  Every entry is written before it is read, so no
  * clearing is needed between calls.
@@ -408,6 +414,20 @@ int xx_exact_grid(const int *n_max, int *n_out);
 #define XX_NOALLOC_MAX_ROWS 16384
 int xx_energy_from_vx_noalloc(int nk, int n_tgt, int npw_max, const int *npw, const void *c_tgt,
                               const double *w_tgt, const void *vx, double *ex_out, void *stream);
+
+/*
+ * Measured CUDA-core fused-multiply-add rate of the current device, in TFLOP/s
+ * (two flops per FMA): the denominator of the ALU rooflines of the benchmark
+ * (FP32 for the mixed-precision passes, FP64 for the all-FP64 path).  The
+ * paper has no counterpart; this is a measurement helper, not part of the
+ * exchange method.  Launches 6 short kernels (8 x SMs CTAs of 256 threads, 8
+ * independent FMA chains of 4096 steps per thread) on stream, times the last 5
+ * with CUDA events and waits for them (blocking).  Allocates no device memory.
+ *   precision: XX_FP32_MIXED (FP32 FMA) or XX_FP64 (FP64 FMA);
+ *   tflops_out: host double.
+ * Returns XX_ERR_INVALID_ARGUMENT, XX_ERR_NO_DEVICE, XX_ERR_CUDA or XX_OK.
+ */
+int xx_measure_fma_rate(int precision, double *tflops_out, void *stream);
 
 /* Static description of a status code. */
 const char *xx_status_string(int status);

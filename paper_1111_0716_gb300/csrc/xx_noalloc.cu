@@ -30,13 +30,15 @@ static __device__ __align__(256) double2 xx_noalloc_dots[XX_NOALLOC_MAX_ROWS];
 double2* g_dots_addr[kMaxDevices] = {nullptr};
 std::mutex g_setup_mutex;
 
-// dots[row] = sum_g conj(c[row][g]) vx[row][g]; one CTA per row, fixed-order tree
+// dots[row] = sum_g conj(c[row][g]) vx[row][g]; one CTA per row, fixed-order tree.
+// The basis size comes from device memory the host cannot check, so it is
+// clamped to [0, npw_max]: a bad npw never reads past a row.
 __global__ void __launch_bounds__(kThreads) k_noalloc_dots(const double2* c, const double2* vx,
                                                            const int* npw, int n_tgt, int npw_max,
                                                            double2* dots) {
   __shared__ double re_s[kThreads], im_s[kThreads];
   const int row = blockIdx.x;
-  const int n = npw[row / n_tgt];
+  const int n = min(max(npw[row / n_tgt], 0), npw_max);
   const double2* a = c + (long long)row * npw_max;
   const double2* b = vx + (long long)row * npw_max;
   double re = 0.0, im = 0.0;

@@ -38,7 +38,7 @@ EXPORTS = ("xx_create", "xx_destroy", "xx_apply", "xx_apply_range", "xx_energy",
            "xx_apply_backward", "xx_sync", "xx_set_batch", "xx_profile_enable",
            "xx_profile_read", "xx_plan_info", "xx_status_string", "xx_exact_grid",
            "xx_energy_from_vx_noalloc", "xx_run_many", "xx_apply_vjp", "xx_set_option",
-           "xx_strain_derivative")
+           "xx_strain_derivative", "xx_measure_fma_rate")
 XX_OPT_PAIR_SYMMETRY = 0
 XX_OPT_REAL_GAMMA = 1
 XX_OPT_TMA_PASS_B = 2
@@ -109,6 +109,7 @@ def load(path: Optional[str] = None):
     lib.xx_strain_derivative.argtypes = [P, P, P, I, P, P, P]
     lib.xx_status_string.argtypes = [I]
     lib.xx_exact_grid.argtypes = [P, P]
+    lib.xx_measure_fma_rate.argtypes = [I, P, P]
     lib.xx_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name not in ("xx_status_string",):
@@ -328,7 +329,7 @@ def xx_strain_derivative(plan, c, w, n_b, dex_deps, ex_out=None, stream=None):
     _check(load().xx_strain_derivative(plan, co(c, "c", n_b), wo(w, "w", n_b), int(n_b),
                                        _dptr(dex_deps, "dex_deps", "f64", 9),
                                        _dptr(ex_out, "ex_out", "f64", 1), _stream_ptr(stream)),
-           "xx_strain_derivative")
+           "xx_strain_derivative", "xx_measure_fma_rate")
 
 
 def xx_set_option(plan, option: int, value: int):
@@ -360,6 +361,14 @@ def xx_exact_grid(n_max) -> int:
     out = np.zeros(1, dtype=np.int32)
     _check(load().xx_exact_grid(_np_ptr(nm), _np_ptr(out)), "xx_exact_grid")
     return int(out[0])
+
+
+def xx_measure_fma_rate(precision: int, stream=None) -> float:
+    """Measured FMA rate (TFLOP/s) of the current device in FP32 or FP64 (blocking)."""
+    out = np.zeros(1, dtype=np.float64)
+    _check(load().xx_measure_fma_rate(int(precision), _np_ptr(out), _stream_ptr(stream)),
+           "xx_measure_fma_rate")
+    return float(out[0])
 
 
 def xx_plan_info(plan) -> dict:

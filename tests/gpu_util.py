@@ -7,6 +7,24 @@ from paper_1111_0716_gb300 import synth  # noqa: F401
 FP32_TOL = 1e-5     # max|dV_x c| <= 1e-5 max|V_x c|, |dE_x| <= 1e-5 |E_x| (mixed precision)
 FP64_TOL = 1e-11    # the all-FP64 path
 
+# Achieved errors against the FP64 oracle (or a closed form), one entry per
+# checked result: (workload, precision, quantity, error, tolerance).  The
+# conftest prints them after the run, and writes them as JSON to the path in
+# XX_PARITY_JSON when that is set.
+PARITY = []
+
+
+def record(workload, prec, quantity, err, tol):
+    """Note an achieved error and return it (for the assertion that follows)."""
+    name = {0: "fp32-mixed", 1: "fp64"}.get(prec, str(prec))
+    PARITY.append((str(workload), name, str(quantity), float(err), float(tol)))
+    return float(err)
+
+
+def rel_err(x, ref):
+    """|x - ref| / |ref| for scalars."""
+    return abs(x - ref) / abs(ref)
+
 
 def need_gpu():
     torch = pytest.importorskip("torch")

@@ -66,8 +66,9 @@ def test_real_gamma_matches_oracle(gpu, oracle_mod, oracle_refs, name, sym, prec
     ref = oracle_refs(name, wl)
     e_ref, _ = oracle_mod.energy_from_vx(wl, ref)
     vx, e = run(xx, wl, prec, True, sym=sym, batch=(3, 2))
-    assert gu.rel_max(vx, ref) <= tol
-    assert abs(e - e_ref) <= tol * abs(e_ref)
+    w = "real Gamma %s%s" % (name, " sym" if sym else "")
+    assert gu.record(w, prec, "max|dVx|/max|Vx|", gu.rel_max(vx, ref), tol) <= tol
+    assert gu.record(w, prec, "|dE_x|/|E_x|", gu.rel_err(e, e_ref), tol) <= tol
 
 
 @pytest.mark.parametrize("prec,tol", [(0, gu.FP32_TOL), (1, gu.FP64_TOL)])

@@ -52,11 +52,14 @@ def test_strain_derivative_matches_finite_differences(gpu, oracle_mod, kernel):
     assert abs(e64 - e_ref) <= 1e-11 * abs(e_ref)
     assert np.abs(d64 - d64.T).max() <= 1e-13 * np.abs(d64).max()
     scale = np.abs(d64).max()
+    w = "rhombo 16^3 strain " + ("screened" if kernel == synth.KERNEL_HSE else "Coulomb")
     for al, be in [(0, 0), (1, 1), (2, 2), (1, 2), (0, 1)]:
         fd = oracle_fd(oracle_mod, wl, al, be)
-        assert abs(d64[al, be] - fd) <= 1e-8 * scale
+        assert gu.record(w, 1, "dE/deps_%d%d vs oracle FD" % (al, be), abs(d64[al, be] - fd) / scale,
+                         1e-8) <= 1e-8
     d32, e32 = gpu_strain(xx, wl, 0)
-    assert np.abs(d32 - d64).max() <= gu.FP32_TOL * scale
+    assert gu.record(w, 0, "dE/deps max|d32-d64|/max|d64|", np.abs(d32 - d64).max() / scale,
+                     gu.FP32_TOL) <= gu.FP32_TOL
     assert abs(e32 - e64) <= gu.FP32_TOL * abs(e64)
 
 

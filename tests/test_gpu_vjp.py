@@ -54,11 +54,14 @@ def test_vjp_matches_finite_differences_of_oracle(gpu, oracle_mod, make):
         d = masked_random(rng, wl, wl.c_tgt.shape)
         fd = (loss(c_tgt=wl.c_tgt + h * d) - loss(c_tgt=wl.c_tgt - h * d)) / (2 * h)
         an = 2.0 * np.real(np.vdot(d, gt))
-        assert abs(fd - an) <= 1e-9 * max(abs(an), np.abs(gt).max())
+        w = "VJP " + wl.name
+        err = abs(fd - an) / max(abs(an), np.abs(gt).max())
+        assert gu.record(w, 1, "dL/dc_tgt* vs oracle FD", err, 1e-9) <= 1e-9
         d = masked_random(rng, wl, wl.c_occ.shape)
         fd = (loss(c_occ=wl.c_occ + h * d) - loss(c_occ=wl.c_occ - h * d)) / (2 * h)
         an = 2.0 * np.real(np.vdot(d, go))
-        assert abs(fd - an) <= 1e-9 * max(abs(an), np.abs(go).max())
+        err = abs(fd - an) / max(abs(an), np.abs(go).max())
+        assert gu.record(w, 1, "dL/dc_occ* vs oracle FD", err, 1e-9) <= 1e-9
 
 
 def test_vjp_mixed_precision_matches_fp64(gpu):
@@ -67,8 +70,10 @@ def test_vjp_mixed_precision_matches_fp64(gpu):
     ybar = masked_random(np.random.default_rng(5), wl, wl.c_tgt.shape)
     gt64, go64 = gpu_vjp(xx, wl, ybar, 1)
     gt32, go32 = gpu_vjp(xx, wl, ybar, 0)
-    assert gu.rel_max(gt32, gt64) <= gu.FP32_TOL
-    assert gu.rel_max(go32, go64) <= gu.FP32_TOL
+    assert gu.record("VJP " + wl.name, 0, "dL/dc_tgt* vs FP64 path", gu.rel_max(gt32, gt64),
+                     gu.FP32_TOL) <= gu.FP32_TOL
+    assert gu.record("VJP " + wl.name, 0, "dL/dc_occ* vs FP64 path", gu.rel_max(go32, go64),
+                     gu.FP32_TOL) <= gu.FP32_TOL
 
 
 def test_autograd_apply_function(gpu, oracle_mod):
