@@ -24,8 +24,11 @@ Printed as one JSON line (rank 0):
                 operator is exact (60^3; same V_x c and E_x up to rounding)
   alpha_boron   the alpha-boron-sized workload (48^3, 64 k-points, 1.77 M pairs)
   --impl reference  times the oracle as the reference arm.
-Multi-GPU (torchrun): each rank runs an independent workload (its own seed),
-weak scaling; value = all ranks' pairs / max-over-ranks time.
+Multi-GPU (torchrun): one workload sharded over the ranks by k-point blocks
+{k, q} (xx_set_shard): every step, rank 0 broadcasts the orbitals (NCCL), each
+rank applies the blocks it owns, the partial V_x c are all-reduced and the E_x
+shares summed in rank order; strong scaling, value = the workload's pairs / the
+max-over-ranks time.
 """
 from __future__ import annotations
 
@@ -133,15 +136,17 @@ def recorded_traffic(kernel, batch):
     return d.get("bytes_per_launch", {}).get(kernel)
 
 
-def batch_schedule(nk, n_occ, n_tgt, TA, TJ, G_max=1, sym=True, cross=True):
+def batch_schedule(nk, n_occ, n_tgt, TA, TJ, G_max=1, sym=True, cross=True, owned=None):
     """The band-pair launches of one xx_energy call with shared grids, in the
     host loop's order: (kind, targets, occupied) with kind "full" (passes A, B,
     C) or "mirrored" (passes A, B, C and the role-swapped pass C).  G_max is the
     plan's q_per_batch: that many k-points' whole occupied sets share a batch;
-    target batches are cut at n_occ (the split of the grids' layout)."""
+    target batches are cut at n_occ (the split of the grids' layout).  owned(k, q):
+    whether the plan's shard owns block {k, q} (None: every block)."""
     out = []
     T = min(TA, TJ)
     sym = sym and n_occ > 1
+    own = owned or (lambda k, q: True)
 
     def run_q(q_lo, q_hi, a_lo, a_hi, mirrored):
         if a_lo >= a_hi:
@@ -160,21 +165,34 @@ def batch_schedule(nk, n_occ, n_tgt, TA, TJ, G_max=1, sym=True, cross=True):
             q0 += G
 
     for k in range(nk):
+        def run_owned(q_lo, q_hi, a_lo, a_hi, mirrored):
+            q = q_lo
+            while q < q_hi:
+                if not own(k, q):
+                    q += 1
+                    continue
+                q_end = q + 1
+                while q_end < q_hi and own(k, q_end):
+                    q_end += 1
+                run_q(q, q_end, a_lo, a_hi, mirrored)
+                q = q_end
+
         if not sym:
-            run_q(0, nk, 0, n_tgt, False)
+            run_owned(0, nk, 0, n_tgt, False)
             continue
-        for i0 in range(0, n_occ, T):
-            for j0 in range(i0, n_occ, T):
-                out.append(("mirrored" if j0 > i0 else "full", min(T, n_occ - i0),
-                            min(T, n_occ - j0)))
-        run_q(k, k + 1, n_occ, n_tgt, False)
+        if own(k, k):
+            for i0 in range(0, n_occ, T):
+                for j0 in range(i0, n_occ, T):
+                    out.append(("mirrored" if j0 > i0 else "full", min(T, n_occ - i0),
+                                min(T, n_occ - j0)))
+            run_q(k, k + 1, n_occ, n_tgt, False)
         if cross:
-            run_q(0, k, n_occ, n_tgt, False)
-            run_q(k + 1, nk, 0, n_occ, True)
-            run_q(k + 1, nk, n_occ, n_tgt, False)
+            run_owned(0, k, n_occ, n_tgt, False)
+            run_owned(k + 1, nk, 0, n_occ, True)
+            run_owned(k + 1, nk, n_occ, n_tgt, False)
         else:
-            run_q(0, k, 0, n_tgt, False)
-            run_q(k + 1, nk, 0, n_tgt, False)
+            run_owned(0, k, 0, n_tgt, False)
+            run_owned(k + 1, nk, 0, n_tgt, False)
     return out
 
 
@@ -460,20 +478,33 @@ def main():
         if world > 1:
             dist.barrier()
 
-    wl = synth.beta_boron(seed=3 + rank)
+    wl = synth.beta_boron()
     pairs = wl.pair_count()
     plan = xx.Plan.from_workload(wl, precision=xx.XX_FP32_MIXED)
+    if world > 1:
+        plan.set_shard(rank, world)
     stream = torch.cuda.current_stream()
-    c = torch.from_numpy(wl.c_tgt).cuda()
+    # rank 0 holds the orbitals; the others receive them every step
+    c = torch.from_numpy(wl.c_tgt).cuda() if rank == 0 else \
+        torch.empty(wl.c_tgt.shape, dtype=torch.complex128, device="cuda")
     w = torch.from_numpy(wl.w_tgt).cuda()
     vx = torch.empty_like(c)
     ex = torch.empty(2, dtype=torch.float64, device="cuda")
+    ex_all = torch.empty(2 * world, dtype=torch.float64, device="cuda")
 
     # the occupied orbitals are the leading n_occ target bands (ld = n_tgt)
     w_occ = torch.from_numpy(wl.w_occ).cuda()
 
     def step():
+        if world > 1:
+            dist.broadcast(c, src=0)                   # orbital distribution
         xx.xx_energy(plan.handle, c, c.shape[1], w_occ, wl.n_occ, c, w, c.shape[1], vx, ex)
+        if world > 1:
+            dist.all_reduce(vx)                        # partial V_x c of every rank's blocks
+            dist.all_gather_into_tensor(ex_all, ex)
+            ex.copy_(ex_all[0:2])
+            for r in range(1, world):                  # E_x shares added in rank order
+                ex.add_(ex_all[2 * r:2 * r + 2])
 
     for _ in range(args.warmup):
         step()
@@ -506,7 +537,7 @@ def main():
         tt = torch.tensor([t], dtype=torch.float64, device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t = float(tt.item())
-    value = world * pairs * args.steps / t
+    value = pairs * args.steps / t
 
     # end to end through the public API with pinned host buffers
     c_h = torch.from_numpy(wl.c_tgt).pin_memory()
@@ -516,12 +547,14 @@ def main():
     ex_h = torch.empty(2, dtype=torch.float64).pin_memory()
 
     def e2e_step():
-        c.copy_(c_h, non_blocking=True)
+        if rank == 0:
+            c.copy_(c_h, non_blocking=True)
         w.copy_(w_h, non_blocking=True)
         w_occ.copy_(wo_h, non_blocking=True)
-        xx.xx_energy(plan.handle, c, c.shape[1], w_occ, wl.n_occ, c, w, c.shape[1], vx, ex)
-        vx_h.copy_(vx, non_blocking=True)
-        ex_h.copy_(ex, non_blocking=True)
+        step()
+        if rank == 0:
+            vx_h.copy_(vx, non_blocking=True)
+            ex_h.copy_(ex, non_blocking=True)
 
     e2e_steps = max(1, min(args.steps, 2))
     e2e_step()
@@ -546,7 +579,12 @@ def main():
     # device time during the timed steps, against the measured HBM copy rate
     hbm, peak_kind = peaks()
     TA, TJ = info["targets_per_batch"], info["occupied_per_batch"]
-    sched = batch_schedule(wl.nk, wl.n_occ, wl.n_tgt, TA, TJ, info["q_per_batch"])
+    owner = xx.xx_shard_blocks(wl.nk, wl.n_occ, wl.n_tgt, world)
+
+    def owned(k, q):
+        k, q = min(k, q), max(k, q)
+        return owner[k * wl.nk - k * (k - 1) // 2 + (q - k)] == rank
+    sched = batch_schedule(wl.nk, wl.n_occ, wl.n_tgt, TA, TJ, info["q_per_batch"], owned=owned)
     transformed = sum(ta * tj for _, ta, tj in sched)
     if transformed * args.steps != pairs_step_transformed:
         raise RuntimeError("launch schedule model (%d pairs) disagrees with the library (%d)"
@@ -586,24 +624,28 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name + " (beta-boron-sized rhombohedral cell)", "grid": 96,
                        "nk": wl.nk, "n_occ": wl.n_occ, "n_tgt": wl.n_tgt,
-                       "pairs_per_step": pairs, "precision": "FP32 FFTs and products, FP64 "
+                       "pairs_per_step": pairs,
+                       "parallelism": ("1 GPU" if world == 1 else
+                                       "%d GPUs, k-point blocks {k, q} sharded, orbitals broadcast "
+                                       "and V_x c all-reduced every step (NCCL)" % world),
+                       "precision": "FP32 FFTs and products, FP64 "
                        "accumulation, kernel table and reductions",
                        "pairs_counted": "logical (k, a, q, j) applications; each occupied pair "
                        "of the blocks (k, q) and (q, k) is transformed once (W_qj,ka = "
                        "conj W_ka,qj): %d transforms per step" % (pairs_step_transformed // args.steps),
                        "batch": [TA, TJ], "l2": "inputs larger than L2 (orbital grids %.1f GB)"
                        % (wl.nk * wl.n_tgt * 96 ** 3 * 8 / 1e9), "E_x": e_x},
-            "e2e": {"value": world * pairs * e2e_steps / t_e2e, "unit": UNIT,
+            "e2e": {"value": pairs * e2e_steps / t_e2e, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roofline, "kernel_time_share": kernel_share,
             "peak_workspace_gb": info["peak_workspace_bytes"] / 1e9}
     if clk:
         line["clocks"] = clk
 
-    if rank == 0 and not args.no_fp64:
+    if rank == 0 and world == 1 and not args.no_fp64:
         # all-FP64 GPU path on one target k-point at the production batch shape: target
         # k=0, 64 target bands x all 160 occupied bands x 8 q (81,920 pairs)
         p64 = xx.Plan.from_workload(wl, precision=xx.XX_FP64)
@@ -648,13 +690,13 @@ def main():
         p64.close()
         p32.close()
 
-    if rank == 0 and not args.no_real:
+    if rank == 0 and world == 1 and not args.no_real:
         line["real_gamma"] = real_gamma_leg(xx, torch, stream)
 
-    if rank == 0 and not args.no_exact_grid:
+    if rank == 0 and world == 1 and not args.no_exact_grid:
         line["exact_grid"] = exact_grid_leg(xx, torch, wl, stream, e_x)
 
-    if rank == 0 and not args.no_alpha:
+    if rank == 0 and world == 1 and not args.no_alpha:
         line["alpha_boron"] = alpha_boron_leg(xx, torch, stream, hbm)
 
     if rank == 0 and args.with_vjp:

@@ -346,6 +346,33 @@ int xx_set_option(xx_plan plan, int option, long long value);
  * the automatic choice.  Takes effect at the next call. */
 int xx_set_batch(xx_plan plan, int targets_per_batch, int occupied_per_batch);
 
+/*
+ * Sharding over GPUs (one process per GPU), after the paper's distribution of
+ * the exchange loops over k-points and bands across MPI ranks (Sec. "Our
+ * Implementation").  The unit is the unordered k-point block {k, q}: every
+ * band pair of targets at k with occupied bands at q, and (the pair symmetry
+ * W_qj,ka = conj W_ka,qj) of targets at q with occupied bands at k.  A block's
+ * contributions add into V_x c of k and of q, so a plan set to shard s of n
+ * computes, in xx_apply / xx_apply_range / xx_energy / xx_energy_range and the
+ * dE/dc* of xx_apply_backward, the partial V_x c and partial E_x of the blocks
+ * assigned to s; summing the n partial results (an all-reduce of V_x c, a sum
+ * of the n E_x shares) gives the full operator, because every block is
+ * assigned to exactly one shard.  Every shard needs every occupied orbital
+ * (the caller distributes them, e.g. a broadcast) and writes V_x c for every
+ * target.  The assignment balances the band-pair transforms of the blocks
+ * (greedy, largest block first, deterministic: the same on every rank).
+ * xx_set_shard(plan, 0, 1) (the default) computes every block.  While n > 1,
+ * dE/dmu (xx_apply_backward with dmu_out), xx_strain_derivative and
+ * xx_apply_vjp return XX_ERR_INVALID_ARGUMENT.
+ */
+int xx_set_shard(xx_plan plan, int shard, int n_shards);
+
+/* The block assignment itself, host only: owner_out[b] (host int array of
+ * nk (nk + 1) / 2) = shard of block b, with b = k nk - k (k - 1) / 2 + (q - k)
+ * for k <= q.  Returns XX_ERR_INVALID_ARGUMENT for nk < 1, negative band
+ * counts, n_shards < 1 or a NULL owner_out. */
+int xx_shard_blocks(int nk, int n_occ, int n_tgt, int n_shards, int *owner_out);
+
 /* Kernel classes of the per-kernel timing (xx_profile_read). */
 #define XX_PROF_PASS_A 0          /* codensity + forward xy FFT */
 #define XX_PROF_PASS_B 1          /* z FFT, kernel multiply, inverse z FFT */

@@ -292,6 +292,9 @@ struct xx_plan_s {
   bool real_gamma = false;     // XX_OPT_REAL_GAMMA
   bool gamma_closed = false;   // one k-point at Gamma whose basis holds -G for every G
   int ta_last = 0, tj_last = 0, g_last = 1;
+  // xx_set_shard: this plan computes the contributions of the (k, q) blocks that
+  // the block assignment gives to shard `shard` of `n_shards` (1: every block)
+  int shard = 0, n_shards = 1;
   // Layout of the shared orbital grids (occupied = leading target bands): the
   // occupied bands of every k-point first ([nk][split]), then the remaining
   // targets ([nk][n_tgt - split]), so the occupied grids of consecutive
@@ -636,6 +639,44 @@ const char* grid_ptr(xx_plan p, bool shared, int q, int j, int n_occ, int n_tgt)
 int run_apply_real(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, int n_occ,
                    const void* c_tgt, int n_tgt, void* vx_out, cudaStream_t s);
 
+// Index of the unordered k-point block {k, q}, k <= q, in the upper triangle
+// (row-major): 0 .. nk (nk + 1) / 2 - 1.
+int block_index(int nk, int k, int q) {
+  if (k > q) std::swap(k, q);
+  return k * nk - k * (k - 1) / 2 + (q - k);
+}
+
+// Owner shard of every block {k, q}: longest-processing-time greedy on the
+// band-pair transforms of a block (the k = q square counted once per pair; a
+// k != q block's occupied square once, its targets past the occupied set
+// against both k-points), blocks taken in decreasing cost, ties by index, each
+// to the least-loaded shard (ties: lowest shard).  Deterministic.
+void assign_blocks(int nk, int n_occ, int n_tgt, int n_shards, std::vector<int>& owner) {
+  const int nb = nk * (nk + 1) / 2;
+  owner.assign(nb, 0);
+  if (n_shards <= 1) return;
+  const long long rest = (long long)(n_tgt > n_occ ? n_tgt - n_occ : 0) * n_occ;
+  std::vector<std::pair<long long, int>> order;
+  for (int k = 0; k < nk; ++k)
+    for (int q = k; q < nk; ++q) {
+      const long long cost = k == q ? (long long)n_occ * (n_occ + 1) / 2 + rest
+                                    : (long long)n_occ * n_occ + 2 * rest;
+      order.push_back({cost, block_index(nk, k, q)});
+    }
+  std::stable_sort(order.begin(), order.end(), [](const std::pair<long long, int>& a,
+                                                  const std::pair<long long, int>& b) {
+    return a.first != b.first ? a.first > b.first : a.second < b.second;
+  });
+  std::vector<long long> load(n_shards, 0);
+  for (const auto& b : order) {
+    int best = 0;
+    for (int r = 1; r < n_shards; ++r)
+      if (load[r] < load[best]) best = r;
+    owner[b.second] = best;
+    load[best] += b.first;
+  }
+}
+
 // The band-pair passes of one batch, each bracketed for per-class timing;
 // pass A counts the batch's pairs.
 void run_pass_a(xx_plan p, const PairArgs& a, cudaStream_t s) {
@@ -759,7 +800,12 @@ int seg_batch(xx_plan p, const SegBatch& b, cudaStream_t s) {
 // real: take the real-orbital Gamma path (plan option XX_OPT_REAL_GAMMA)
 int run_apply(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, const double* w_occ,
               int n_occ, const void* c_tgt, int n_tgt, void* vx_out, bool real, cudaStream_t s) {
-  if (real) return run_apply_real(p, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, vx_out, s);
+  if (real) {
+    // one k-point: its single block {0, 0} belongs to shard 0
+    if (p->n_shards > 1 && p->shard != 0)
+      return cuda_status(cudaMemsetAsync(vx_out, 0, (size_t)kn * n_tgt * p->npw_max * 16, s));
+    return run_apply_real(p, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, vx_out, s);
+  }
   const bool shared = (c_occ == c_tgt && ld_occ == n_tgt && k0 == 0 && kn == p->nk);
   int st = build_grids(p, k0, kn, c_occ, ld_occ, n_occ, c_tgt, n_tgt, shared, s);
   if (st) return st;
@@ -804,6 +850,10 @@ int run_apply(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, const do
     return (double2*)p->acc.p + split_index(split, p->nk, n_tgt, k, b) * nn;
   };
   const int T = TJ < TA ? TJ : TA;
+  // sharded plan: only the blocks {k, q} this shard owns
+  std::vector<int> owner;
+  assign_blocks(p->nk, n_occ, n_tgt, p->n_shards, owner);
+  auto owned = [&](int k, int q) { return owner[block_index(p->nk, k, q)] == p->shard; };
   for (int kk = 0; kk < kn; ++kk) {
     const int k = k0 + kk;
     char name[40];
@@ -849,9 +899,24 @@ int run_apply(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, const do
       }
       return XX_OK;
     };
+    // run_q over the maximal runs of q in [q_lo, q_hi) whose block {k, q} this shard owns
+    auto run_owned = [&](int q_lo, int q_hi, int a_lo, int a_hi, bool mirrored) -> int {
+      for (int q = q_lo; q < q_hi;) {
+        if (!owned(k, q)) {
+          ++q;
+          continue;
+        }
+        int q_end = q + 1;
+        while (q_end < q_hi && owned(k, q_end)) ++q_end;
+        const int e = run_q(q, q_end, a_lo, a_hi, mirrored);
+        if (e) return e;
+        q = q_end;
+      }
+      return XX_OK;
+    };
     if (!sym) {
-      if ((st = run_q(0, p->nk, 0, n_tgt, false))) return st;
-    } else {
+      if ((st = run_owned(0, p->nk, 0, n_tgt, false))) return st;
+    } else if (owned(k, k)) {
       // k = q: tiles I <= J of the occupied square (tiles J > I receive
       // -(w_a/N_k) u_a conj(W_aj) through the role-swapped pass C), then the
       // targets past the occupied set
@@ -874,14 +939,16 @@ int run_apply(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, const do
         }
       }
       if ((st = run_q(k, k + 1, n_occ, n_tgt, false))) return st;
+    }
+    if (sym) {
       if (cross) {
         // blocks q < k: their occupied squares ran with block (q, k)
-        if ((st = run_q(0, k, n_occ, n_tgt, false))) return st;
-        if ((st = run_q(k + 1, p->nk, 0, n_occ, true))) return st;
-        if ((st = run_q(k + 1, p->nk, n_occ, n_tgt, false))) return st;
+        if ((st = run_owned(0, k, n_occ, n_tgt, false))) return st;
+        if ((st = run_owned(k + 1, p->nk, 0, n_occ, true))) return st;
+        if ((st = run_owned(k + 1, p->nk, n_occ, n_tgt, false))) return st;
       } else {
-        if ((st = run_q(0, k, 0, n_tgt, false))) return st;
-        if ((st = run_q(k + 1, p->nk, 0, n_tgt, false))) return st;
+        if ((st = run_owned(0, k, 0, n_tgt, false))) return st;
+        if ((st = run_owned(k + 1, p->nk, 0, n_tgt, false))) return st;
       }
     }
     // every contribution to the targets of k is in (blocks (k', k) with k' < k
@@ -1593,6 +1660,7 @@ int xx_apply_backward(xx_plan p, const void* c, const double* w, int n_b, const 
                       double grad_ex, void* dc_out, double* dmu_out, void* stream) {
   if (!p || n_b < 0 || !std::isfinite(grad_ex)) return XX_ERR_INVALID_ARGUMENT;
   if (dmu_out && p->kernel != XX_KERNEL_HSE) return XX_ERR_INVALID_ARGUMENT;
+  if (dmu_out && p->n_shards > 1) return XX_ERR_INVALID_ARGUMENT;   // dE/dmu is not sharded
   cudaStream_t s = (cudaStream_t)stream;
   if (n_b == 0) {
     if (dmu_out) return cuda_status(cudaMemsetAsync(dmu_out, 0, sizeof(double), s));
@@ -1621,7 +1689,7 @@ int xx_apply_backward(xx_plan p, const void* c, const double* w, int n_b, const 
 
 int xx_strain_derivative(xx_plan p, const void* c, const double* w, int n_b, double* dex_deps,
                          double* ex_out, void* stream) {
-  if (!p || n_b < 0 || bad_ptr(dex_deps)) return XX_ERR_INVALID_ARGUMENT;
+  if (!p || n_b < 0 || bad_ptr(dex_deps) || p->n_shards > 1) return XX_ERR_INVALID_ARGUMENT;
   cudaStream_t s = (cudaStream_t)stream;
   if (n_b == 0) {
     cudaError_t e = cudaMemsetAsync(dex_deps, 0, 9 * sizeof(double), s);
@@ -1680,7 +1748,7 @@ int xx_apply_vjp(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, 
                  const void* c_tgt, int n_tgt, const void* ybar, void* grad_tgt_out,
                  void* grad_occ_out, void* stream) {
   Range r("xx vjp");
-  if (!p || n_occ < 0 || n_tgt < 0) return XX_ERR_INVALID_ARGUMENT;
+  if (!p || n_occ < 0 || n_tgt < 0 || p->n_shards > 1) return XX_ERR_INVALID_ARGUMENT;
   if (ld_occ == 0) ld_occ = n_occ;
   if (ld_occ < n_occ) return XX_ERR_INVALID_ARGUMENT;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1782,6 +1850,21 @@ int xx_set_option(xx_plan p, int option, long long value) {
     default:
       return XX_ERR_INVALID_ARGUMENT;
   }
+}
+
+int xx_set_shard(xx_plan p, int shard, int n_shards) {
+  if (!p || n_shards < 1 || shard < 0 || shard >= n_shards) return XX_ERR_INVALID_ARGUMENT;
+  p->shard = shard;
+  p->n_shards = n_shards;
+  return XX_OK;
+}
+
+int xx_shard_blocks(int nk, int n_occ, int n_tgt, int n_shards, int* owner_out) {
+  if (nk < 1 || n_occ < 0 || n_tgt < 0 || n_shards < 1 || !owner_out) return XX_ERR_INVALID_ARGUMENT;
+  std::vector<int> owner;
+  assign_blocks(nk, n_occ, n_tgt, n_shards, owner);
+  std::copy(owner.begin(), owner.end(), owner_out);
+  return XX_OK;
 }
 
 int xx_set_batch(xx_plan p, int targets_per_batch, int occupied_per_batch) {

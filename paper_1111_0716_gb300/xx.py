@@ -38,7 +38,7 @@ EXPORTS = ("xx_create", "xx_destroy", "xx_apply", "xx_apply_range", "xx_energy",
            "xx_apply_backward", "xx_sync", "xx_set_batch", "xx_profile_enable",
            "xx_profile_read", "xx_plan_info", "xx_status_string", "xx_exact_grid",
            "xx_energy_from_vx_noalloc", "xx_run_many", "xx_apply_vjp", "xx_set_option",
-           "xx_strain_derivative", "xx_measure_fma_rate")
+           "xx_strain_derivative", "xx_measure_fma_rate", "xx_set_shard", "xx_shard_blocks")
 XX_OPT_PAIR_SYMMETRY = 0
 XX_OPT_REAL_GAMMA = 1
 XX_OPT_TMA_PASS_B = 2
@@ -110,6 +110,8 @@ def load(path: Optional[str] = None):
     lib.xx_status_string.argtypes = [I]
     lib.xx_exact_grid.argtypes = [P, P]
     lib.xx_measure_fma_rate.argtypes = [I, P, P]
+    lib.xx_set_shard.argtypes = [P, I, I]
+    lib.xx_shard_blocks.argtypes = [I, I, I, I, P]
     lib.xx_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name not in ("xx_status_string",):
@@ -329,7 +331,7 @@ def xx_strain_derivative(plan, c, w, n_b, dex_deps, ex_out=None, stream=None):
     _check(load().xx_strain_derivative(plan, co(c, "c", n_b), wo(w, "w", n_b), int(n_b),
                                        _dptr(dex_deps, "dex_deps", "f64", 9),
                                        _dptr(ex_out, "ex_out", "f64", 1), _stream_ptr(stream)),
-           "xx_strain_derivative", "xx_measure_fma_rate")
+           "xx_strain_derivative")
 
 
 def xx_set_option(plan, option: int, value: int):
@@ -361,6 +363,18 @@ def xx_exact_grid(n_max) -> int:
     out = np.zeros(1, dtype=np.int32)
     _check(load().xx_exact_grid(_np_ptr(nm), _np_ptr(out)), "xx_exact_grid")
     return int(out[0])
+
+
+def xx_set_shard(plan, shard: int, n_shards: int):
+    _check(load().xx_set_shard(plan, int(shard), int(n_shards)), "xx_set_shard")
+
+
+def xx_shard_blocks(nk: int, n_occ: int, n_tgt: int, n_shards: int) -> np.ndarray:
+    """Owner shard of each k-point block {k <= q} (upper triangle, row-major)."""
+    out = np.zeros(nk * (nk + 1) // 2, dtype=np.int32)
+    _check(load().xx_shard_blocks(int(nk), int(n_occ), int(n_tgt), int(n_shards), _np_ptr(out)),
+           "xx_shard_blocks")
+    return out
 
 
 def xx_measure_fma_rate(precision: int, stream=None) -> float:
@@ -418,6 +432,10 @@ class Plan:
 
     def profile_read(self, reset: bool = True) -> dict:
         return xx_profile_read(self.handle, reset)
+
+    def set_shard(self, shard: int, n_shards: int):
+        """Compute only the k-point blocks assigned to shard `shard` of `n_shards`."""
+        xx_set_shard(self.handle, shard, n_shards)
 
     def set_pair_symmetry(self, enable: bool):
         xx_set_option(self.handle, XX_OPT_PAIR_SYMMETRY, 1 if enable else 0)

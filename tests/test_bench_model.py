@@ -68,3 +68,29 @@ def test_byte_model_without_symmetry_is_48_bytes_per_point():
     assert b["pass_b"] == 16 * n3 * pairs
     assert b["pass_c"] == 16 * n3 * pairs + 32 * n3 * per_target
     assert sum(b.values()) == 48 * n3 * pairs + 40 * n3 * per_target
+
+
+@pytest.mark.parametrize("nk,n_occ,n_tgt,TA,TJ,G", [(8, 160, 192, 64, 80, 1), (8, 4, 6, 6, 4, 8),
+                                                     (5, 3, 5, 5, 3, 2), (3, 5, 7, 2, 4, 1)])
+@pytest.mark.parametrize("world", [2, 3, 8])
+def test_sharded_schedules_add_up_to_the_whole(nk, n_occ, n_tgt, TA, TJ, G, world):
+    """Each block {k, q} belongs to one shard (the library's assignment, host code):
+    the shards' schedules transform, between them, exactly the unsharded pairs."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1111_0716_gb300 import xx
+    owner = xx.xx_shard_blocks(nk, n_occ, n_tgt, world)
+
+    def owned_by(r):
+        def f(k, q):
+            k, q = min(k, q), max(k, q)
+            return owner[k * nk - k * (k - 1) // 2 + (q - k)] == r
+        return f
+    whole = sum(ta * tj for _, ta, tj in bench.batch_schedule(nk, n_occ, n_tgt, TA, TJ, G))
+    parts = [sum(ta * tj for _, ta, tj in bench.batch_schedule(nk, n_occ, n_tgt, TA, TJ, G,
+                                                               owned=owned_by(r)))
+             for r in range(world)]
+    assert sum(parts) == whole
+    if nk == 8 and n_occ == 160:
+        # the beta-boron workload: every shard within 5 % of the mean
+        assert max(parts) <= 1.05 * whole / world

@@ -61,6 +61,7 @@ def test_dc_matches_finite_differences_of_gpu_energy(gpu):
     plan.close()
     rng = np.random.default_rng(4)
     h = 1e-4
+    worst = 0.0
     for _ in range(16):
         d = rng.standard_normal(wl.c_tgt.shape) + 1j * rng.standard_normal(wl.c_tgt.shape)
         d[:, :, wl.npw[0]:] = 0
@@ -68,9 +69,9 @@ def test_dc_matches_finite_differences_of_gpu_energy(gpu):
         fd = (gpu_energy(xx, torch, wl, wl.c_tgt + h * d) -
               gpu_energy(xx, torch, wl, wl.c_tgt - h * d)) / (2 * h)
         an = 2.0 * np.real(np.vdot(d, grad))
-        err = abs(fd - an) / max(abs(an), 1e-3 * np.abs(grad).max())
-        assert gu.record("tiny cubic 24^3 (8/8, Gamma)", 1, "dE/dc* vs central FD (h=1e-4)", err,
-                         1e-7) <= 1e-7
+        worst = max(worst, abs(fd - an) / max(abs(an), 1e-3 * np.abs(grad).max()))
+    assert gu.record("tiny cubic 24^3 (8/8, Gamma)", 1, "dE/dc* vs central FD, worst of 16", worst,
+                     1e-7) <= 1e-7
 
 
 def test_dmu_matches_finite_differences_of_gpu_energy(gpu):

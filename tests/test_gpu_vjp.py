@@ -50,18 +50,19 @@ def test_vjp_matches_finite_differences_of_oracle(gpu, oracle_mod, make):
         vx = oracle_mod.apply(wl, c_occ=c_occ, c_tgt=c_tgt)
         return float(np.real(np.vdot(pvec, vx)))
     h = 1e-3
+    worst_t = worst_o = 0.0
     for _ in range(4):
         d = masked_random(rng, wl, wl.c_tgt.shape)
         fd = (loss(c_tgt=wl.c_tgt + h * d) - loss(c_tgt=wl.c_tgt - h * d)) / (2 * h)
         an = 2.0 * np.real(np.vdot(d, gt))
-        w = "VJP " + wl.name
-        err = abs(fd - an) / max(abs(an), np.abs(gt).max())
-        assert gu.record(w, 1, "dL/dc_tgt* vs oracle FD", err, 1e-9) <= 1e-9
+        worst_t = max(worst_t, abs(fd - an) / max(abs(an), np.abs(gt).max()))
         d = masked_random(rng, wl, wl.c_occ.shape)
         fd = (loss(c_occ=wl.c_occ + h * d) - loss(c_occ=wl.c_occ - h * d)) / (2 * h)
         an = 2.0 * np.real(np.vdot(d, go))
-        err = abs(fd - an) / max(abs(an), np.abs(go).max())
-        assert gu.record(w, 1, "dL/dc_occ* vs oracle FD", err, 1e-9) <= 1e-9
+        worst_o = max(worst_o, abs(fd - an) / max(abs(an), np.abs(go).max()))
+    w = "VJP " + wl.name
+    assert gu.record(w, 1, "dL/dc_tgt* vs oracle FD, worst of 4", worst_t, 1e-9) <= 1e-9
+    assert gu.record(w, 1, "dL/dc_occ* vs oracle FD, worst of 4", worst_o, 1e-9) <= 1e-9
 
 
 def test_vjp_mixed_precision_matches_fp64(gpu):
