@@ -497,10 +497,10 @@ def main():
 
     def step():
         if world > 1:
-            dist.broadcast(c, src=0)                   # orbital distribution
+            dist.broadcast(torch.view_as_real(c), src=0)   # orbital distribution
         xx.xx_energy(plan.handle, c, c.shape[1], w_occ, wl.n_occ, c, w, c.shape[1], vx, ex)
         if world > 1:
-            dist.all_reduce(vx)                        # partial V_x c of every rank's blocks
+            dist.all_reduce(torch.view_as_real(vx))        # partial V_x c of every rank's blocks
             dist.all_gather_into_tensor(ex_all, ex)
             ex.copy_(ex_all[0:2])
             for r in range(1, world):                  # E_x shares added in rank order
