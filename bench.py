@@ -217,6 +217,26 @@ def pass_bytes_per_step(wl, schedule, elem=8):
     return {"pass_a": a, "pass_b": b, "pass_c": c}
 
 
+def distribute_orbitals(c):
+    """Rank 0's orbital coefficients (complex tensor) to every rank."""
+    import torch
+    import torch.distributed as dist
+    dist.broadcast(torch.view_as_real(c), src=0)
+
+
+def combine_shards(vx, ex, ex_parts):
+    """Sum the ranks' partial V_x c (in place, every rank) and their E_x shares,
+    the shares added in rank order so the total does not depend on the
+    collective's reduction order (ex_parts: one 2-vector per rank, scratch)."""
+    import torch
+    import torch.distributed as dist
+    dist.all_reduce(torch.view_as_real(vx))
+    dist.all_gather(ex_parts, ex)
+    ex.copy_(ex_parts[0])
+    for part in ex_parts[1:]:
+        ex.add_(part)
+
+
 def run_oracle_sample(wl, n_occ_sample, want_vx=False):
     """The FP64 oracle on target (k=0, a=0), all q, the first n_occ_sample occupied bands."""
     from oracle import oracle
@@ -490,21 +510,18 @@ def main():
     w = torch.from_numpy(wl.w_tgt).cuda()
     vx = torch.empty_like(c)
     ex = torch.empty(2, dtype=torch.float64, device="cuda")
-    ex_all = torch.empty(2 * world, dtype=torch.float64, device="cuda")
 
     # the occupied orbitals are the leading n_occ target bands (ld = n_tgt)
     w_occ = torch.from_numpy(wl.w_occ).cuda()
 
+    ex_parts = [torch.empty(2, dtype=torch.float64, device="cuda") for _ in range(world)]
+
     def step():
         if world > 1:
-            dist.broadcast(torch.view_as_real(c), src=0)   # orbital distribution
+            distribute_orbitals(c)
         xx.xx_energy(plan.handle, c, c.shape[1], w_occ, wl.n_occ, c, w, c.shape[1], vx, ex)
         if world > 1:
-            dist.all_reduce(torch.view_as_real(vx))        # partial V_x c of every rank's blocks
-            dist.all_gather_into_tensor(ex_all, ex)
-            ex.copy_(ex_all[0:2])
-            for r in range(1, world):                  # E_x shares added in rank order
-                ex.add_(ex_all[2 * r:2 * r + 2])
+            combine_shards(vx, ex, ex_parts)
 
     for _ in range(args.warmup):
         step()

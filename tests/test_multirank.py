@@ -155,3 +155,42 @@ def test_two_gloo_ranks_block_shards_reproduce_the_operator(tmp_path, oracle_mod
     assert abs(float(total) - float(ref)) <= 1e-13 * abs(float(ref))
     assert float(err_v) <= 1e-13
     assert int(used) == world
+
+
+def _bench_collectives_worker(rank, world, port, out_path):
+    import torch
+    import torch.distributed as dist
+
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    rng = np.random.default_rng(5)
+    c_all = rng.standard_normal((2, 3, 7)) + 1j * rng.standard_normal((2, 3, 7))
+    c = torch.from_numpy(c_all.copy() if rank == 0 else np.zeros_like(c_all))
+    bench.distribute_orbitals(c)
+    ok_c = bool(np.array_equal(c.numpy(), c_all))
+    # a partial "V_x c" and E_x share per rank
+    vx = torch.from_numpy((rank + 1) * c_all)
+    ex = torch.tensor([-(rank + 1.5), 0.25 * rank], dtype=torch.float64)
+    parts = [torch.empty(2, dtype=torch.float64) for _ in range(world)]
+    bench.combine_shards(vx, ex, parts)
+    want_vx = sum(r + 1 for r in range(world)) * c_all
+    want_ex = [sum(-(r + 1.5) for r in range(world)), sum(0.25 * r for r in range(world))]
+    ok = ok_c and np.allclose(vx.numpy(), want_vx, rtol=1e-15, atol=0) and \
+        ex.tolist() == want_ex
+    with open(out_path + ".%d" % rank, "w") as f:
+        f.write("1" if ok else "0")
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_bench_collectives_on_two_gloo_ranks(tmp_path):
+    """bench.py's orbital broadcast and shard combination (the data path of its
+    multi-GPU step) on CPU tensors."""
+    out = str(tmp_path / "coll")
+    world = 2
+    mp.start_processes(_bench_collectives_worker, args=(world, _free_port(), out), nprocs=world,
+                       start_method="spawn", join=True)
+    for r in range(world):
+        assert open(out + ".%d" % r).read() == "1"
