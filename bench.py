@@ -23,6 +23,8 @@ Printed as one JSON line (rank 0):
   exact_grid    the same workload with the plan on the smallest grid on which the
                 operator is exact (60^3; same V_x c and E_x up to rounding)
   alpha_boron   the alpha-boron-sized workload (48^3, 64 k-points, 1.77 M pairs)
+  sweep_cells   six uneven Gamma cells in one launch per band-pair pass, against
+                one plan per cell on concurrent streams
   --impl reference  times the oracle as the reference arm.
 Multi-GPU (torchrun): one workload sharded over the ranks by k-point blocks
 {k, q} (xx_set_shard): every step, rank 0 broadcasts the orbitals (NCCL), each
@@ -436,6 +438,46 @@ def alpha_boron_leg(xx, torch, stream, hbm, reps=2):
                       "mean of %d steps" % (wl.name, wl.pair_count(), reps)}
 
 
+def sweep_leg(xx, torch, stream, reps=3):
+    """The six uneven sweep cells (32^3 ... 80^3, 16 ... 96 bands, Gamma; 17,472 pairs):
+    one launch per band-pair pass over all cells (xx_run_batched) against one plan per
+    cell on concurrent streams (xx_run_many), FP32-mixed."""
+    from paper_1111_0716_gb300 import synth
+    cells = [synth.sweep_cell(i) for i in range(len(synth.SWEEP_GRIDS))]
+    plans, jobs = [], []
+    for wl in cells:
+        plan = xx.Plan.from_workload(wl, precision=xx.XX_FP32_MIXED, workspace_cap=48 << 30)
+        c = torch.from_numpy(wl.c_tgt).cuda()
+        jobs.append({"plan": plan, "c_occ": c, "ld_occ": c.shape[1],
+                     "w_occ": torch.from_numpy(wl.w_occ).cuda(), "c_tgt": c,
+                     "w_tgt": torch.from_numpy(wl.w_tgt).cuda(), "vx_out": torch.empty_like(c),
+                     "ex_out": torch.empty(2, dtype=torch.float64, device="cuda")})
+        plans.append(plan)
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, fn in (("batched", xx.xx_run_batched), ("streams", xx.xx_run_many)):
+        fn(jobs, stream=stream)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            g0.record(stream)
+            fn(jobs, stream=stream)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(g0.elapsed_time(g1) / 1e3)
+        out[name] = float(np.median(ts))
+    for plan in plans:
+        plan.sync(timeout_s=60.0, stream=stream)
+        plan.close()
+    pairs = sum(wl.pair_count() for wl in cells)
+    return {"value": pairs / out["batched"], "unit": UNIT, "streams_same_cells": pairs / out["streams"],
+            "ms_batched": 1e3 * out["batched"], "ms_streams": 1e3 * out["streams"],
+            "sample": "six Gamma cells 32^3 ... 80^3 with 16 ... 96 bands (%d pairs), FP32-mixed, "
+                      "one launch per band-pair pass over all cells vs one plan per cell on its own "
+                      "stream, median of %d" % (pairs, reps)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -451,6 +493,8 @@ def main():
     ap.add_argument("--no-exact-grid", action="store_true",
                     help="skip the smallest-exact-grid leg")
     ap.add_argument("--no-alpha", action="store_true", help="skip the alpha-boron-sized leg")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the six-cell sweep leg (one launch per pass vs streams)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one slice of the workload (k=0, 64 targets x 80 occupied bands, "
                          "all q: one launch per pass in the benchmark's batch shape) once and "
@@ -712,6 +756,9 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_exact_grid:
         line["exact_grid"] = exact_grid_leg(xx, torch, wl, stream, e_x)
+
+    if rank == 0 and world == 1 and not args.no_sweep:
+        line["sweep_cells"] = sweep_leg(xx, torch, stream)
 
     if rank == 0 and world == 1 and not args.no_alpha:
         line["alpha_boron"] = alpha_boron_leg(xx, torch, stream, hbm)

@@ -237,6 +237,30 @@ typedef struct {
 int xx_run_many(int n_jobs, const xx_job *jobs, void *stream);
 
 /*
+ * Run independent Gamma-only jobs (one plan each, one k-point per plan, e.g.
+ * cells with different FFT grid lengths) with ONE launch per band-pair pass
+ * covering every band-pair batch of every job: a table of batches (grid
+ * pointers, grid length, pruned box, batch shape) goes to each launch, and
+ * every CTA runs the pass of its batch's grid length.  This replaces the
+ * paper's streams for small structures (xx_run_many) by a single work list.
+ * Per job, on the plan's own stream (which first waits for the work queued
+ * on `stream`): sphere -> grid and the kernel table; then, on `stream`, per
+ * round the passes A, B, C and, for mirrored k = q tiles, the role-swapped
+ * pass C (one launch each for all jobs; batches that add into the same
+ * targets add into private accumulator planes, summed per target in batch
+ * order afterwards); then per job on its own stream the sums, grid -> sphere
+ * and, when ex_out is set, E_x; `stream` finally waits for every job.
+ * A round holds as many of each job's batches as its plan's workspace cap
+ * allows; with enough workspace (the caller's workspace_cap) there is one
+ * round.  Results equal xx_energy / xx_apply on each job up to the order of
+ * FP32 summation within a batch (the batches are the same as theirs, so the
+ * results are identical when the batch shapes are).  All plans must share one
+ * precision, be unsharded and have nk = 1; a plan may appear once.  Returns
+ * XX_ERR_INVALID_ARGUMENT for a violated requirement, else the first error.
+ */
+int xx_run_batched(int n_jobs, const xx_job *jobs, void *stream);
+
+/*
  * Vector-Jacobian product (the paper has none; the derivative of the Eq. 2
  * loops' output) of y = V_x[c_occ] c_tgt (xx_apply's output) for a
  * real loss L with cotangent ybar = dL/dy* (Wirtinger; device complex128

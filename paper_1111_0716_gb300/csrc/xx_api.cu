@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "../../include/xx.h"
+#include "xx_cells.cuh"
 #include "xx_launch.cuh"
 
 namespace xx {
@@ -307,7 +308,7 @@ struct xx_plan_s {
   void* d_tw64 = nullptr;
   int* d_err = nullptr;
   DevBuf u_tgt, u_occ, inter, acc, vt, dvt, box, stage, dots, partial, dmu_acc, vx_tmp, u_bar,
-      stab, cpack, wpair, acc2;
+      stab, cpack, wpair, acc2, cells_tab;
   size_t ws_bytes = 0, peak_bytes = 0;
   long long launches = 0;
   long long pairs = 0;          // band pairs (or packed slots) through pass A so far
@@ -1564,7 +1565,7 @@ int xx_destroy(xx_plan p) {
   cudaDeviceSynchronize();
   DevBuf* bufs[] = {&p->u_tgt, &p->u_occ, &p->inter, &p->acc, &p->vt, &p->dvt, &p->box,
                     &p->stage, &p->dots, &p->partial, &p->dmu_acc, &p->vx_tmp, &p->u_bar,
-                    &p->stab, &p->cpack, &p->wpair, &p->acc2};
+                    &p->stab, &p->cpack, &p->wpair, &p->acc2, &p->cells_tab};
   for (DevBuf* b : bufs) release(*b);
   if (p->d_miller) cudaFree(p->d_miller);
   if (p->d_npw) cudaFree(p->d_npw);
@@ -1742,6 +1743,280 @@ int xx_run_many(int n_jobs, const xx_job* jobs, void* stream) {
     if (e != cudaSuccess && status == XX_OK) status = cuda_status(e);
   }
   return status;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One band-pair batch of one job in the batched path: its pair arguments
+// (inter set per round) and whether its role-swapped pass C runs too.  One
+// launch holds batches that add into the same targets, so every batch adds
+// into private accumulator planes of its own (a0, ta: its pass C targets; j0,
+// tj and ct_plane0: its role-swapped targets), summed per target afterwards in
+// batch order.
+struct BatchedItem {
+  PairArgs a;
+  PairArgs ct;       // role-swapped arguments (mirrored items)
+  bool mirrored = false;
+  size_t pairs = 0;
+  int a0 = 0, ta = 0, j0 = 0, tj = 0;
+  long long c_plane0 = 0, ct_plane0 = 0;   // first private plane of each side
+};
+
+// acc[row] = sum over the row's private planes in table order; grid (chunks, rows)
+__global__ void k_sum_planes(const double2* priv, const int* row_ptr, const int* planes, long long nn,
+                             double2* acc) {
+  const int row = blockIdx.y;
+  const int b = row_ptr[row], e = row_ptr[row + 1];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn;
+       i += (long long)gridDim.x * blockDim.x) {
+    double2 sum = make_double2(0.0, 0.0);
+    for (int k = b; k < e; ++k) {
+      const double2 v = priv[(long long)planes[k] * nn + i];
+      sum.x += v.x;
+      sum.y += v.y;
+    }
+    acc[(long long)row * nn + i] = sum;
+  }
+}
+
+// The batches of one Gamma-only job, as run_apply forms them: k = q tiles I <= J
+// of the occupied square with the pair symmetry (tiles J > I mirrored), then the
+// targets past the occupied set; without it, every target batch against every
+// occupied batch.
+void batched_items(xx_plan p, const xx_job& j, bool shared, std::vector<BatchedItem>& out) {
+  int TA, TJ;
+  batch_shape(p, j.n_tgt, j.n_occ, &TA, &TJ);
+  long long planes = 0;
+  auto add = [&](int a0, int ta, int j0, int tj, bool mirrored) {
+    BatchedItem it;
+    it.a = pair_args(p, ta, tj);
+    it.a.u_tgt = grid_ptr(p, true, 0, a0, j.n_occ, j.n_tgt);
+    it.a.u_occ = grid_ptr(p, shared, 0, j0, j.n_occ, j.n_tgt);
+    it.a.w_occ = j.w_occ + j0;
+    it.mirrored = mirrored;
+    it.a0 = a0;
+    it.ta = ta;
+    it.j0 = j0;
+    it.tj = tj;
+    it.c_plane0 = planes;
+    planes += ta;
+    if (mirrored) {
+      it.ct = it.a;
+      it.ct.w_tgt = j.w_occ + a0;
+      it.ct.w_occ = nullptr;
+      it.ct_plane0 = planes;
+      planes += tj;
+    }
+    it.pairs = (size_t)ta * tj;
+    out.push_back(it);
+  };
+  const int n_occ = j.n_occ, n_tgt = j.n_tgt;
+  if (shared && p->pair_symmetry && n_occ > 1) {
+    const int T = TJ < TA ? TJ : TA;
+    for (int i0 = 0; i0 < n_occ; i0 += T)
+      for (int j0 = i0; j0 < n_occ; j0 += T)
+        add(i0, std::min(T, n_occ - i0), j0, std::min(T, n_occ - j0), j0 > i0);
+    for (int a0 = n_occ; a0 < n_tgt; a0 += TA)
+      for (int j0 = 0; j0 < n_occ; j0 += TJ) add(a0, std::min(TA, n_tgt - a0), j0, std::min(TJ, n_occ - j0), false);
+  } else {
+    for (int a0 = 0; a0 < n_tgt; a0 += TA)
+      for (int j0 = 0; j0 < n_occ; j0 += TJ) add(a0, std::min(TA, n_tgt - a0), j0, std::min(TJ, n_occ - j0), false);
+  }
+}
+
+// Fork: each job's own stream waits for the work queued on `caller`.
+int fork_streams(int n_jobs, const xx_job* jobs, cudaStream_t caller) {
+  for (int i = 0; i < n_jobs; ++i) {
+    xx_plan p = jobs[i].plan;
+    cudaError_t e = cudaSuccess;
+    if (!p->own_stream) e = cudaStreamCreateWithFlags(&p->own_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !p->ev_fork) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !p->ev_join) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_fork, caller);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->own_stream, p->ev_fork, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_status(e);
+    }
+  }
+  return XX_OK;
+}
+
+// Join: `caller` waits for the work queued on every job's own stream.
+int join_streams(int n_jobs, const xx_job* jobs, cudaStream_t caller) {
+  for (int i = 0; i < n_jobs; ++i) {
+    xx_plan p = jobs[i].plan;
+    cudaError_t e = cudaEventRecord(p->ev_join, p->own_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, p->ev_join, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_status(e);
+    }
+  }
+  return XX_OK;
+}
+
+// One batched launch of `pass` over the given items (each with its plan's grid
+// length); splits into several launches past kMaxCellItems items.
+int launch_batched(int pass, bool fp64, const std::vector<std::pair<const PairArgs*, int>>& items,
+                   cudaStream_t s) {
+  for (size_t first = 0; first < items.size(); first += kMaxCellItems) {
+    const size_t count = std::min(items.size() - first, (size_t)kMaxCellItems);
+    CellItems ci{};
+    ci.n_items = (int)count;
+    long long ctas = 0;
+    int threads = 32;
+    size_t smem = 0;
+    for (size_t i = 0; i < count; ++i) {
+      const PairArgs& a = *items[first + i].first;
+      const int n = items[first + i].second;
+      ci.item[i].a = a;
+      ci.item[i].n = n;
+      ci.item[i].cta0 = ctas;
+      ctas += cell_item_ctas(pass, a, n);
+      threads = std::max(threads, cell_body_threads(pass, fp64, n));
+      smem = std::max(smem, cell_body_smem(pass, fp64, n, a.P1, a.P3));
+    }
+    const cudaError_t e = launch_cell_pass(pass, fp64, ci, ctas, threads, smem, s);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return XX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int xx_run_batched(int n_jobs, const xx_job* jobs, void* stream) {
+  Range r("xx run batched");
+  if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return XX_ERR_INVALID_ARGUMENT;
+  if (n_jobs == 0) return XX_OK;
+  const int prec = jobs[0].plan ? jobs[0].plan->prec : -1;
+  for (int i = 0; i < n_jobs; ++i) {
+    const xx_job& j = jobs[i];
+    xx_plan p = j.plan;
+    if (!p || p->prec != prec || p->nk != 1 || p->n_shards > 1 || !cell_length_supported(p->N))
+      return XX_ERR_INVALID_ARGUMENT;
+    for (int k = 0; k < i; ++k)
+      if (jobs[k].plan == p) return XX_ERR_INVALID_ARGUMENT;
+    if (j.n_occ < 0 || j.n_tgt < 0 || j.ld_occ < 0 || (j.ld_occ > 0 && j.ld_occ < j.n_occ))
+      return XX_ERR_INVALID_ARGUMENT;
+    if (j.n_tgt > 0 && (bad_ptr(j.c_tgt) || bad_ptr(j.vx_out))) return XX_ERR_INVALID_ARGUMENT;
+    if (j.n_tgt > 0 && j.n_occ > 0 && (bad_ptr(j.c_occ) || bad_ptr(j.w_occ))) return XX_ERR_INVALID_ARGUMENT;
+    if (j.ex_out && j.n_tgt > 0 && bad_ptr(j.w_tgt)) return XX_ERR_INVALID_ARGUMENT;
+  }
+  cudaStream_t caller = (cudaStream_t)stream;
+  const bool fp64 = prec == XX_FP64;
+  int st;
+  // per job, on its own stream: orbital grids, kernel table, zeroed accumulators
+  // and band-pair batches
+  if ((st = fork_streams(n_jobs, jobs, caller))) return st;
+  std::vector<std::vector<BatchedItem>> items(n_jobs);
+  for (int i = 0; i < n_jobs; ++i) {
+    const xx_job& j = jobs[i];
+    xx_plan p = j.plan;
+    cudaStream_t s = p->own_stream;
+    if (j.n_tgt == 0 || j.n_occ == 0) continue;
+    const int ld = j.ld_occ > 0 ? j.ld_occ : j.n_occ;
+    const bool shared = j.c_occ == j.c_tgt && ld == j.n_tgt;
+    if ((st = build_grids(p, 0, 1, j.c_occ, ld, j.n_occ, j.c_tgt, j.n_tgt, shared, s))) return st;
+    if ((st = kernel_table_for(p, 0, 0, false, s))) return st;
+    if ((st = ensure(p, p->acc, (size_t)j.n_tgt * n3(p) * 16))) return st;
+    batched_items(p, j, shared, items[i]);
+    // private accumulator planes of the batches (zeroed), and the table of the
+    // planes that add up to each target, in batch order
+    const BatchedItem& last = items[i].back();
+    const long long planes = last.mirrored ? last.ct_plane0 + last.tj : last.c_plane0 + last.ta;
+    const size_t priv_bytes = (size_t)planes * n3(p) * 16;
+    if ((st = ensure(p, p->acc2, priv_bytes))) return st;
+    if ((st = cuda_status(cudaMemsetAsync(p->acc2.p, 0, priv_bytes, s)))) return st;
+    std::vector<std::vector<int>> rows(j.n_tgt);
+    for (BatchedItem& it : items[i]) {
+      it.a.acc = (double2*)p->acc2.p + it.c_plane0 * n3(p);
+      for (int a = 0; a < it.ta; ++a) rows[it.a0 + a].push_back((int)(it.c_plane0 + a));
+      if (it.mirrored) {
+        it.ct.acc = (double2*)p->acc2.p + it.ct_plane0 * n3(p);
+        for (int b = 0; b < it.tj; ++b) rows[it.j0 + b].push_back((int)(it.ct_plane0 + b));
+      }
+    }
+    std::vector<int> tab(1, 0);
+    for (const auto& row : rows) tab.push_back(tab.back() + (int)row.size());
+    for (const auto& row : rows) tab.insert(tab.end(), row.begin(), row.end());
+    if ((st = ensure(p, p->cells_tab, tab.size() * sizeof(int)))) return st;
+    // pageable source: the copy has taken the data when the call returns
+    if ((st = cuda_status(cudaMemcpyAsync(p->cells_tab.p, tab.data(), tab.size() * sizeof(int),
+                                          cudaMemcpyHostToDevice, s))))
+      return st;
+  }
+  if ((st = join_streams(n_jobs, jobs, caller))) return st;
+  // rounds: each job's batches in order, as many per round as its workspace cap
+  // holds (one round when every job's batches fit at once); in a launch the
+  // batches run largest first (grid points x pairs), which shortens its tail
+  std::vector<size_t> next(n_jobs, 0);
+  cudaStream_t s = caller;
+  for (;;) {
+    std::vector<std::pair<const PairArgs*, int>> all, mirrored;
+    for (int i = 0; i < n_jobs; ++i) {
+      xx_plan p = jobs[i].plan;
+      const size_t per_pair = inter_pair_bytes(p);
+      size_t used = 0, first = next[i], end = next[i];
+      while (end < items[i].size() && (end == first || (used + items[i][end].pairs) * per_pair <= p->cap))
+        used += items[i][end++].pairs;
+      if (end == first) continue;
+      if ((st = ensure(p, p->inter, used * per_pair))) return st;
+      size_t off = 0;
+      for (size_t k = first; k < end; ++k) {
+        BatchedItem& it = items[i][k];
+        it.a.inter = (char*)p->inter.p + off * per_pair;
+        it.ct.inter = it.a.inter;
+        off += it.pairs;
+        all.push_back({&it.a, p->N});
+        if (it.mirrored) mirrored.push_back({&it.ct, p->N});
+        p->pairs += (long long)it.pairs;
+      }
+      next[i] = end;
+    }
+    if (all.empty()) break;
+    auto larger = [](const std::pair<const PairArgs*, int>& x, const std::pair<const PairArgs*, int>& y) {
+      const double wx = (double)x.second * x.second * x.second * x.first->TA * x.first->TJ;
+      const double wy = (double)y.second * y.second * y.second * y.first->TA * y.first->TJ;
+      return wx > wy;
+    };
+    std::stable_sort(all.begin(), all.end(), larger);
+    std::stable_sort(mirrored.begin(), mirrored.end(), larger);
+    if ((st = launch_batched(kCellPassA, fp64, all, s))) return st;
+    if ((st = launch_batched(kCellPassB, fp64, all, s))) return st;
+    if ((st = launch_batched(kCellPassC, fp64, all, s))) return st;
+    if (!mirrored.empty() && (st = launch_batched(kCellPassCT, fp64, mirrored, s))) return st;
+    jobs[0].plan->launches += mirrored.empty() ? 3 : 4;
+  }
+  // per job, on its own stream: the sums of the private planes, grid -> sphere and E_x
+  if ((st = fork_streams(n_jobs, jobs, caller))) return st;
+  for (int i = 0; i < n_jobs; ++i) {
+    const xx_job& j = jobs[i];
+    xx_plan p = j.plan;
+    cudaStream_t s = p->own_stream;
+    if (j.n_tgt == 0) {
+      if (j.ex_out && (st = cuda_status(cudaMemsetAsync(j.ex_out, 0, 2 * sizeof(double), s)))) return st;
+      continue;
+    }
+    if (j.n_occ == 0) {
+      if ((st = cuda_status(cudaMemsetAsync(j.vx_out, 0, (size_t)j.n_tgt * p->npw_max * 16, s)))) return st;
+    } else {
+      const int* tab = (const int*)p->cells_tab.p;
+      const long long nn = n3(p);
+      const int chunks = (int)std::min<long long>((nn + 255) / 256, 1024);
+      k_sum_planes<<<dim3(chunks, j.n_tgt), 256, 0, s>>>((const double2*)p->acc2.p, tab, tab + j.n_tgt + 1,
+                                                         nn, (double2*)p->acc.p);
+      if ((st = launched(p, 1))) return st;
+      if ((st = grid_to_sphere(p, 0, (double2*)p->acc.p, j.n_tgt, (double2*)j.vx_out, s))) return st;
+    }
+    if (j.ex_out && (st = run_energy_reduce(p, 0, 1, j.c_tgt, j.w_tgt, j.n_tgt, j.vx_out, j.ex_out, s)))
+      return st;
+  }
+  return join_streams(n_jobs, jobs, caller);
 }
 
 int xx_apply_vjp(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ, int n_occ,

@@ -144,6 +144,16 @@ struct NoHook {
   __device__ __forceinline__ void operator()() const {}
 };
 
+// Barrier among the first NT threads of the CTA (barrier 0 with a thread
+// count).  Every building block below synchronises with it, so a transform of
+// NT threads can run inside a larger CTA whose other threads have left (the
+// batched launches over cells of different grid lengths); with NT equal to the
+// block size it is the ordinary CTA barrier.
+template <int NT> __device__ __forceinline__ void bsync() {
+  static_assert(NT % 32 == 0, "barriers count whole warps");
+  asm volatile("bar.sync 0, %0;" ::"n"(NT) : "memory");
+}
+
 // Cooperative L1 prefetch of [p, p + bytes): one 128-byte line per thread.
 __device__ __forceinline__ void prefetch_l1(const void* p, long long bytes) {
   const long long line = (long long)threadIdx.x * 128;
@@ -199,7 +209,7 @@ __device__ __forceinline__ void plane_forward(const cplx<T>* tw, cplx<T>* s0, cp
         s0[y * LD + k1 * S + n2] = tw_mul<false>(r[k1], G::REG_TW ? twr[k1] : tw[n2 * k1]);
     }
   }
-  __syncthreads();
+  bsync<NT>();
   after_x1();
   // x, step 2: length-B DFTs, output at natural f_x positions
   if constexpr (G::DB) {
@@ -231,14 +241,14 @@ __device__ __forceinline__ void plane_forward(const cplx<T>* tw, cplx<T>* s0, cp
         for (int n2 = 0; n2 < B; ++n2) hold[n2] = s0[row * LD + k1 * S + n2];
         dft<B, false>(hold);
       }
-      __syncthreads();
+      bsync<NT>();
       if (it < N * A) {
 #pragma unroll
         for (int k2 = 0; k2 < B; ++k2) sy[row * LD + k1 + A * k2] = hold[k2];
       }
     }
   }
-  __syncthreads();
+  bsync<NT>();
   // y, step 1: warp-uniform n2, lanes over kept f_x columns; in place
   const int nkb = (P1 + 31) >> 5;
 #pragma unroll 1
@@ -254,7 +264,7 @@ __device__ __forceinline__ void plane_forward(const cplx<T>* tw, cplx<T>* s0, cp
       for (int k1 = 0; k1 < A; ++k1) sy[(k1 * B + n2) * LD + fx] = tw_mul<false>(r[k1], tw[n2 * k1]);
     }
   }
-  __syncthreads();
+  bsync<NT>();
   // y, step 2: warp-uniform k1; kept f_y go to store
 #pragma unroll 1
   for (int u = warp; u < A * nkb; u += NW) {
@@ -273,7 +283,7 @@ __device__ __forceinline__ void plane_forward(const cplx<T>* tw, cplx<T>* s0, cp
     }
   }
   before_end();
-  __syncthreads();
+  bsync<NT>();
 }
 
 // Inverse y then x transform from kept frequencies (load(kyb, kxb)) to the
@@ -318,7 +328,7 @@ __device__ __forceinline__ void plane_inverse(const cplx<T>* tw, const cplx<T>* 
       for (int k1 = 0; k1 < A; ++k1) s0[(k1 * B + n2) * LD + xm] = tw_mul<true>(r[k1], tw[n2 * k1]);
     }
   }
-  __syncthreads();
+  bsync<NT>();
   // y, step 2: warp-uniform k1, in place (row y = k1 + A*k2 lands in row k1*B + k2)
 #pragma unroll 1
   for (int u = warp; u < A * nkb; u += NW) {
@@ -333,7 +343,7 @@ __device__ __forceinline__ void plane_inverse(const cplx<T>* tw, const cplx<T>* 
       for (int k2 = 0; k2 < B; ++k2) s0[(k1 * B + k2) * LD + xm] = r[k2];
     }
   }
-  __syncthreads();
+  bsync<NT>();
   // optional L1 prefetch of what the last step reads (pass C: the u_j plane)
   if (pf_x) prefetch_l1(pf_x, pf_x_bytes);
   // x, step 1: kept f_x of every row in, slot-order out
@@ -374,7 +384,7 @@ __device__ __forceinline__ void plane_inverse(const cplx<T>* tw, const cplx<T>* 
         }
         dft<A, true>(hold);
       }
-      __syncthreads();
+      bsync<NT>();
       if (it < N * B) {
 #pragma unroll
         for (int k1 = 0; k1 < A; ++k1) {
@@ -385,7 +395,7 @@ __device__ __forceinline__ void plane_inverse(const cplx<T>* tw, const cplx<T>* 
       }
     }
   }
-  __syncthreads();
+  bsync<NT>();
   // optional L1 prefetch of the next call's input (pass C: the next plane)
   if (pf_next) prefetch_l1(pf_next, pf_next_bytes);
   // x, step 2: every output to consume
@@ -404,7 +414,7 @@ __device__ __forceinline__ void plane_inverse(const cplx<T>* tw, const cplx<T>* 
       for (int k2 = 0; k2 < B; ++k2) consume(i, k2, y, k1 + A * k2, r[k2]);
     }
   }
-  __syncthreads();
+  bsync<NT>();
 }
 
 // Forward z transform of a row of W pencils: load(z, c) real space,
@@ -432,7 +442,7 @@ __device__ __forceinline__ void pencil_forward(const cplx<T>* tw, cplx<T>* sZ, i
       for (int k1 = 0; k1 < A; ++k1) sZ[(k1 * B + n2) * ld + c] = tw_mul<false>(r[k1], tw[n2 * k1]);
     }
   }
-  __syncthreads();
+  bsync<NT>();
 #pragma unroll 1
   for (int u = warp; u < A * ncb; u += NW) {
     const int k1 = u % A, c = lane + 32 * (u / A);
@@ -475,7 +485,7 @@ __device__ __forceinline__ void pencil_inverse(const cplx<T>* tw, cplx<T>* sZ, i
       for (int k1 = 0; k1 < A; ++k1) sZ[(k1 * B + n2) * ld + c] = tw_mul<true>(r[k1], tw[n2 * k1]);
     }
   }
-  __syncthreads();
+  bsync<NT>();
 #pragma unroll 1
   for (int u = warp; u < A * ncb; u += NW) {
     const int k1 = u % A, c = lane + 32 * (u / A);
@@ -490,14 +500,19 @@ __device__ __forceinline__ void pencil_inverse(const cplx<T>* tw, cplx<T>* sZ, i
   }
 }
 
-template <int N, typename T> __device__ __forceinline__ void load_twiddles(cplx<T>* dst, const void* src) {
-  for (int i = threadIdx.x; i < N; i += blockDim.x) dst[i] = ((const cplx<T>*)src)[i];
+// NT > 0: only the first NT threads take part (stride NT); 0: the whole block
+template <int N, typename T, int NT = 0>
+__device__ __forceinline__ void load_twiddles(cplx<T>* dst, const void* src) {
+  const int stride = NT > 0 ? NT : (int)blockDim.x;
+  for (int i = threadIdx.x; i < N; i += stride) dst[i] = ((const cplx<T>*)src)[i];
 }
 
 // tw2[k1 * B + n2] = tw[n2 * k1] (call after load_twiddles and a barrier)
-template <int N, typename T> __device__ __forceinline__ void make_twiddles2(cplx<T>* tw2, const cplx<T>* tw) {
+template <int N, typename T, int NT = 0>
+__device__ __forceinline__ void make_twiddles2(cplx<T>* tw2, const cplx<T>* tw) {
   constexpr int A = Lay<N>::A, B = Lay<N>::B;
-  for (int i = threadIdx.x; i < A * B; i += blockDim.x) tw2[i] = tw[(i % B) * (i / B)];
+  const int stride = NT > 0 ? NT : (int)blockDim.x;
+  for (int i = threadIdx.x; i < A * B; i += stride) tw2[i] = tw[(i % B) * (i / B)];
 }
 
 template <int N, typename T> constexpr size_t smem_pencil(int W, int P3) {
@@ -508,18 +523,20 @@ template <int N, typename T> constexpr size_t smem_pencil(int W, int P3) {
 
 // Pass A: grid (TA, N); CTA (ta, z) loops over the TJ occupied bands.  One
 // plane buffer, so two CTAs share an SM and overlap each other's barriers.
+// The body takes its CTA's (ta, z) and its shared memory from the caller, so
+// the batched launch over several cells (k_pass_a_cells) runs the same code.
+// DB = true: the two-buffer plane (more threads per plane, no register holds;
+// the batched launches use it at N = 60, whose one-buffer plane needs 480 threads).
 template <int N, typename T> using PassACfg = PlaneCfg<N, T, false>;
-template <int N, typename T>
-__global__ void __launch_bounds__(PassACfg<N, T>::NT, sizeof(T) == 4 ? 2 : 1) k_pass_a(PairArgs p) {
+template <int N, typename T, bool DB = false>
+__device__ __forceinline__ void pass_a_body(const PairArgs& p, int ta, int z, unsigned char* smem_raw) {
   using C = cplx<T>;
-  using G = PassACfg<N, T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using G = PlaneCfg<N, T, DB>;
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* s0 = tw + N;
   C* s1 = s0 + G::BUF;
-  load_twiddles<N, T>(tw, p.tw);
-  __syncthreads();
-  const int ta = blockIdx.x, z = blockIdx.y;
+  load_twiddles<N, T, G::NT>(tw, p.tw);
+  bsync<G::NT>();
   constexpr long long plane = (long long)N * N;
   const C* ua = reinterpret_cast<const C*>(p.u_tgt) + ta * p.u_tgt_stride + z * plane;
   const int LX = p.LX;
@@ -528,25 +545,28 @@ __global__ void __launch_bounds__(PassACfg<N, T>::NT, sizeof(T) == 4 ? 2 : 1) k_
     const C* uj = reinterpret_cast<const C*>(p.u_occ) + tj * p.u_occ_stride + z * plane;
     C* out = reinterpret_cast<C*>(p.inter) +
              ((long long)(ta * p.TJ + tj) * N + z) * (long long)p.P2 * LX;
-    plane_forward<N, T, false>(
+    plane_forward<N, T, DB>(
         tw, s0, s1, p.h1, p.P1, p.h2,
         [&](int y, int x) { return cmulc(uj[y * N + x], ua[y * N + x]); },
         [&](int kyb, int kxb, C v) { out[kyb * LX + kxb] = v; });
   }
 }
+template <int N, typename T>
+__global__ void __launch_bounds__(PassACfg<N, T>::NT, sizeof(T) == 4 ? 2 : 1) k_pass_a(PairArgs p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pass_a_body<N, T>(p, blockIdx.x, blockIdx.y, smem_raw);
+}
 
 // Pass B: grid (P2, TA*TJ); CTA (kyb, pair) transforms its row along z,
 // multiplies by v(k - q + G)/N and transforms back, in place.
 template <int N, int NT, typename T>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_pass_b(PairArgs p) {
+__device__ __forceinline__ void pass_b_body(const PairArgs& p, int kyb, int pair, unsigned char* smem_raw) {
   using C = cplx<T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* sZ = tw + N;
   C* sK = sZ + N * p.P1;
-  load_twiddles<N, T>(tw, p.tw);
-  __syncthreads();
-  const int kyb = blockIdx.x, pair = blockIdx.y;
+  load_twiddles<N, T, NT>(tw, p.tw);
+  bsync<NT>();
   const int P1 = p.P1, P2 = p.P2;
   const int zstride = P2 * p.LX;               // a pair's planes stay within 32-bit offsets
   C* row = reinterpret_cast<C*>(p.inter) + (long long)pair * N * zstride + kyb * p.LX;
@@ -557,12 +577,16 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_pass_b(PairArgs 
         const T s = vt[kzb * (P2 * P1) + c];
         sK[kzb * P1 + c] = s * v;
       });
-  __syncthreads();
+  bsync<NT>();
   pencil_inverse<N, NT, T>(
       tw, sZ, P1, p.h3, [&](int kzb, int c) { return sK[kzb * P1 + c]; },
       [&](int z, int c, C v) { row[z * zstride + c] = v; });
 }
-
+template <int N, int NT, typename T>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_pass_b(PairArgs p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pass_b_body<N, NT, T>(p, blockIdx.x, blockIdx.y, smem_raw);
+}
 // --------------------------------------------- tensor-copy staged pass B --
 //
 // Bulk tensor copies (TMA) with mbarrier completion.  Every wait on an mbarrier
@@ -861,20 +885,18 @@ __global__ void __launch_bounds__(NT) k_pass_b_dmu(PairArgs p) {
 //   acc_a.x += -(1/N_q) (w_2p u_2p W_a,2p + w_2p+1 u_2p+1 W_a,2p+1)
 //            = -(1/N_q) (w_2p Re(u) Re(W) - w_2p+1 Im(u) Im(W)).
 template <int N, typename T, bool PACKED>
-__global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_c(PairArgs p) {
+__device__ __forceinline__ void pass_c_body(const PairArgs& p, int ta, int z, unsigned char* smem_raw) {
   using C = cplx<T>;
   using G = PlaneCfg<N, T>;
   constexpr int A = G::A, B = G::B, NT = G::NT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* tw2 = tw + N;
   C* s0 = tw2 + N;
   C* s1 = s0 + G::BUF;
-  load_twiddles<N, T>(tw, p.tw);
-  __syncthreads();
-  make_twiddles2<N, T>(tw2, tw);
-  __syncthreads();
-  const int ta = blockIdx.x, z = blockIdx.y;
+  load_twiddles<N, T, NT>(tw, p.tw);
+  bsync<NT>();
+  make_twiddles2<N, T, NT>(tw2, tw);
+  bsync<NT>();
   constexpr long long plane = (long long)N * N;
   const int LX = p.LX;
   C acc[G::X2_IT][B];
@@ -936,6 +958,11 @@ __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_c(PairArgs p) {
     }
   }
 }
+template <int N, typename T, bool PACKED>
+__global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_c(PairArgs p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pass_c_body<N, T, PACKED>(p, blockIdx.x, blockIdx.y, smem_raw);
+}
 
 // Pass C with the roles swapped: grid (TJ, N); CTA (tj, z) owns band j of the
 // batch's second index and loops over the TA bands a of its first index,
@@ -946,20 +973,18 @@ __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_c(PairArgs p) {
 // w_j), and the pair symmetry W_qj,ka = conj(W_ka,qj) (f_a = u_a, weight w_a)
 // on k = q tiles and k != q blocks.
 template <int N, typename T>
-__global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_ct(PairArgs p) {
+__device__ __forceinline__ void pass_ct_body(const PairArgs& p, int tj, int z, unsigned char* smem_raw) {
   using C = cplx<T>;
   using G = PlaneCfg<N, T>;
   constexpr int A = G::A, B = G::B, NT = G::NT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* tw2 = tw + N;
   C* s0 = tw2 + N;
   C* s1 = s0 + G::BUF;
-  load_twiddles<N, T>(tw, p.tw);
-  __syncthreads();
-  make_twiddles2<N, T>(tw2, tw);
-  __syncthreads();
-  const int tj = blockIdx.x, z = blockIdx.y;
+  load_twiddles<N, T, NT>(tw, p.tw);
+  bsync<NT>();
+  make_twiddles2<N, T, NT>(tw2, tw);
+  bsync<NT>();
   constexpr long long plane = (long long)N * N;
   const int LX = p.LX;
   const long long pstride = (long long)p.P2 * LX;
@@ -1002,6 +1027,11 @@ __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_ct(PairArgs p) {
       }
     }
   }
+}
+template <int N, typename T>
+__global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_ct(PairArgs p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pass_ct_body<N, T>(p, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // ------------------------------------------------------ kernel table (a2) --

@@ -38,7 +38,8 @@ EXPORTS = ("xx_create", "xx_destroy", "xx_apply", "xx_apply_range", "xx_energy",
            "xx_apply_backward", "xx_sync", "xx_set_batch", "xx_profile_enable",
            "xx_profile_read", "xx_plan_info", "xx_status_string", "xx_exact_grid",
            "xx_energy_from_vx_noalloc", "xx_run_many", "xx_apply_vjp", "xx_set_option",
-           "xx_strain_derivative", "xx_measure_fma_rate", "xx_set_shard", "xx_shard_blocks")
+           "xx_strain_derivative", "xx_measure_fma_rate", "xx_set_shard", "xx_shard_blocks",
+           "xx_run_batched")
 XX_OPT_PAIR_SYMMETRY = 0
 XX_OPT_REAL_GAMMA = 1
 XX_OPT_TMA_PASS_B = 2
@@ -104,6 +105,7 @@ def load(path: Optional[str] = None):
     lib.xx_profile_read.argtypes = [P, P, P, I, I]
     lib.xx_energy_from_vx_noalloc.argtypes = [I, I, I, P, P, P, P, P, P]
     lib.xx_run_many.argtypes = [I, ctypes.POINTER(xx_job), P]
+    lib.xx_run_batched.argtypes = [I, ctypes.POINTER(xx_job), P]
     lib.xx_apply_vjp.argtypes = [P, P, I, P, I, P, I, P, P, P, P]
     lib.xx_set_option.argtypes = [P, I, ctypes.c_longlong]
     lib.xx_strain_derivative.argtypes = [P, P, P, I, P, P, P]
@@ -299,10 +301,7 @@ def xx_apply_vjp(plan, c_occ, ld_occ, w_occ, n_occ, c_tgt, n_tgt, ybar, grad_tgt
            "xx_apply_vjp")
 
 
-def xx_run_many(jobs, stream=None):
-    """jobs: list of dicts with keys plan (Plan), c_occ, w_occ, c_tgt, w_tgt, vx_out, ex_out
-    (ex_out/w_tgt optional) and optional ld_occ; the occupied set is the leading bands when
-    c_occ is c_tgt."""
+def _job_array(jobs):
     arr = (xx_job * len(jobs))()
     for i, j in enumerate(jobs):
         n_occ = j["w_occ"].shape[1]
@@ -319,7 +318,20 @@ def xx_run_many(jobs, stream=None):
         arr[i].n_tgt = int(n_tgt)
         arr[i].vx_out = c(j["vx_out"], "vx_out", n_tgt)
         arr[i].ex_out = _dptr(j.get("ex_out"), "ex_out", "f64", 2)
-    _check(load().xx_run_many(len(jobs), arr, _stream_ptr(stream)), "xx_run_many")
+    return arr
+
+
+def xx_run_many(jobs, stream=None):
+    """jobs: list of dicts with keys plan (Plan), c_occ, w_occ, c_tgt, w_tgt, vx_out, ex_out
+    (ex_out/w_tgt optional) and optional ld_occ; the occupied set is the leading bands when
+    c_occ is c_tgt."""
+    _check(load().xx_run_many(len(jobs), _job_array(jobs), _stream_ptr(stream)), "xx_run_many")
+
+
+def xx_run_batched(jobs, stream=None):
+    """Gamma-only jobs (same keys as xx_run_many) with one launch per band-pair pass."""
+    _check(load().xx_run_batched(len(jobs), _job_array(jobs), _stream_ptr(stream)),
+           "xx_run_batched")
 
 
 def xx_sync(plan, stream=None, timeout_s: float = 0.0):

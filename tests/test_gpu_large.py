@@ -30,6 +30,18 @@ def fp64_target_slice(xx, wl, k, a):
     return out
 
 
+def fp32_target_slice(xx, wl, k, a, tj):
+    """V_x c of target (k, a) alone, FP32-mixed, occupied batches tj bands wide."""
+    plan = xx.Plan.from_workload(wl, precision=0)
+    plan.set_batch(1, tj)
+    co, wo = gu.dev(wl.c_occ), gu.dev(wl.w_occ)
+    vx = plan.apply_range(k, 1, co, wo, gu.dev(wl.c_tgt[k:k + 1, a:a + 1]))
+    plan.sync(timeout_s=600.0)
+    out = vx.cpu().numpy()[0, 0]
+    plan.close()
+    return out
+
+
 def test_alpha_boron_48_mp444(gpu, oracle_mod):
     torch, xx = gpu
     wl = synth.alpha_boron()
@@ -91,6 +103,13 @@ def test_beta_boron_96_gamma222(gpu, oracle_mod):
     v64 = fp64_target_slice(xx, wl, k, a)
     assert gu.record(w, 1, "max|dVx|/max|Vx| target (%d,%d)" % (k, a), gu.rel_max(v64, ref),
                      gu.FP64_TOL) <= gu.FP64_TOL
+    # the FP32 partial sums over an occupied batch before each FP64 add: the
+    # production width (80 occupied per batch) against 8 per batch, same targets
+    for (kk, aa), r in zip(sel, refs):
+        for tj in (80, 8):
+            v = fp32_target_slice(xx, wl, kk, aa, tj)
+            assert gu.record(w, 0, "max|dVx|/max|Vx| (%d,%d), %d occ/batch" % (kk, aa, tj),
+                             gu.rel_max(v, r), t32) <= t32
     # the smallest exact grid (60^3 for n_max = 14) gives the same operator as 96^3
     n = xx.xx_exact_grid(wl.n_max())
     assert n == 60
