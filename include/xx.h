@@ -37,7 +37,11 @@
  * N_i >= 4 n_i + 1 where n_i is the largest |Miller index| along axis i over
  * all basis sets (the paper sizes its FFT grids so that no aliasing occurs);
  * otherwise xx_create returns XX_ERR_GRID_ALIASING.  Supported axis lengths:
- * 24, 32, 40, 48, 60, 64, 72, 80, 96, equal on all three axes.
+ * 24, 32, 40, 48, 60, 64, 72, 80, 96, with at least two of the three equal
+ * (N x N x M in any axis order; the plan relabels the axes internally so the
+ * equal pair spans its planes, which changes nothing in the results or in the
+ * layout of any argument).  Three different lengths return
+ * XX_ERR_UNSUPPORTED_GRID.
  *
  * Ownership: the caller owns every input and output buffer (device memory
  * unless stated otherwise).  The plan owns its derived tables and workspace,

@@ -263,7 +263,9 @@ struct DevBuf {
 
 struct xx_plan_s {
   int device = 0;
-  int N = 0;
+  int N = 0;              // x and y length of the FFT grid (after the axis permutation)
+  int NZ = 0;             // z length
+  int perm[3] = {0, 1, 2};   // plan axis i is the caller's axis perm[i]
   int grid[3] = {0, 0, 0};
   int nk = 0;
   int npw_max = 0;
@@ -301,11 +303,14 @@ struct xx_plan_s {
   // targets ([nk][n_tgt - split]), so the occupied grids of consecutive
   // k-points are contiguous; split = 0: plain [k][n_tgt]
   int split = 0, split_nk = 0, split_ntgt = 0;
-  const KernelTable* kt = nullptr;
+  const KernelTable* kt = nullptr;   // = &kx
+  KernelTable kx;                    // plane kernels of length N, pencil kernels of length NZ
   int* d_miller = nullptr;   // [nk][npw_max][3]
   int* d_npw = nullptr;      // [nk]
   void* d_tw32 = nullptr;
   void* d_tw64 = nullptr;
+  void* d_twz32 = nullptr;   // z twiddles (length NZ)
+  void* d_twz64 = nullptr;
   int* d_err = nullptr;
   DevBuf u_tgt, u_occ, inter, acc, vt, dvt, box, stage, dots, partial, dmu_acc, vx_tmp, u_bar,
       stab, cpack, wpair, acc2, cells_tab;
@@ -374,7 +379,7 @@ bool supported_n(int n) { return kernel_table(n) != nullptr; }
 
 size_t elem_bytes(const xx_plan p) { return p->prec == XX_FP64 ? 16 : 8; }
 
-long long n3(const xx_plan p) { return (long long)p->N * p->N * p->N; }
+long long n3(const xx_plan p) { return (long long)p->N * p->N * p->NZ; }
 
 int P(const xx_plan p, int ax) { return 2 * p->h[ax] + 1; }
 int Q(const xx_plan p, int ax) { return 2 * p->nmax[ax] + 1; }
@@ -386,7 +391,7 @@ int LX(const xx_plan p) { return p->prec == XX_FP64 ? P(p, 0) : (P(p, 0) + 1) & 
 
 // bytes of one band pair's intermediate, [N][P2][LX]
 size_t inter_pair_bytes(const xx_plan p) {
-  return (size_t)p->N * P(p, 1) * LX(p) * (p->prec == XX_FP64 ? 16 : 8);
+  return (size_t)p->NZ * P(p, 1) * LX(p) * (p->prec == XX_FP64 ? 16 : 8);
 }
 
 const KernelSet& kset(const xx_plan p) { return p->prec == XX_FP64 ? p->kt->f64 : p->kt->f32; }
@@ -430,7 +435,7 @@ int sphere_to_grid(xx_plan p, int k, const double2* c, int nb, void* u, cudaStre
   const int chunk = nb < kGridChunk ? nb : kGridChunk;
   int st = ensure(p, p->box, (size_t)chunk * Q1 * Q2 * Q3 * eb);
   if (st) return st;
-  st = ensure(p, p->stage, (size_t)chunk * p->N * Q1 * Q2 * eb);
+  st = ensure(p, p->stage, (size_t)chunk * p->NZ * Q1 * Q2 * eb);
   if (st) return st;
   for (int b0 = 0; b0 < nb; b0 += chunk) {
     const int cb = (nb - b0) < chunk ? (nb - b0) : chunk;
@@ -444,6 +449,8 @@ int sphere_to_grid(xx_plan p, int k, const double2* c, int nb, void* u, cudaStre
     g.stage = p->stage.p;
     g.u = (char*)u + (size_t)b0 * n3(p) * eb;
     g.tw = p->prec == XX_FP64 ? p->d_tw64 : p->d_tw32;
+    g.twz = p->prec == XX_FP64 ? p->d_twz64 : p->d_twz32;
+    g.nz = p->NZ;
     g.n1 = p->nmax[0];
     g.n2 = p->nmax[1];
     g.n3 = p->nmax[2];
@@ -474,7 +481,7 @@ int grid_to_sphere(xx_plan p, int k, const double2* f, int nb, double2* out, cud
   const int chunk = nb < kGridChunk ? nb : kGridChunk;
   int st = ensure(p, p->box, (size_t)chunk * Q1 * Q2 * Q3 * 16);
   if (st) return st;
-  st = ensure(p, p->stage, (size_t)chunk * p->N * Q1 * Q2 * 16);
+  st = ensure(p, p->stage, (size_t)chunk * p->NZ * Q1 * Q2 * 16);
   if (st) return st;
   for (int b0 = 0; b0 < nb; b0 += chunk) {
     const int cb = (nb - b0) < chunk ? (nb - b0) : chunk;
@@ -488,6 +495,8 @@ int grid_to_sphere(xx_plan p, int k, const double2* f, int nb, double2* out, cud
     g.stage = p->stage.p;
     g.f = f + (long long)b0 * n3(p);
     g.tw = p->d_tw64;
+    g.twz = p->d_twz64;
+    g.nz = p->NZ;
     g.n1 = p->nmax[0];
     g.n2 = p->nmax[1];
     g.n3 = p->nmax[2];
@@ -562,6 +571,8 @@ PairArgs pair_args(xx_plan p, int TA, int TJ) {
   a.dvt = p->dvt.p;
   a.partial = (double*)p->partial.p;
   a.tw = p->prec == XX_FP64 ? p->d_tw64 : p->d_tw32;
+  a.twz = p->prec == XX_FP64 ? p->d_twz64 : p->d_twz32;
+  a.nz = p->NZ;
   a.u_tgt_stride = n3(p);
   a.u_occ_stride = n3(p);
   a.TA = TA;
@@ -715,7 +726,7 @@ void run_pass_b(xx_plan p, const PairArgs& a, cudaStream_t s) {
   // of N = 60, 14 % slower
   const bool want = p->tma_pass_b == 2 || (p->tma_pass_b == 1 && 4 * a.P1 <= 3 * p->N);
   PFN_cuTensorMapEncodeTiled_v12000 enc = p->prec == XX_FP32_MIXED && want ? tensor_map_encoder() : nullptr;
-  if (enc && 2 * a.LX <= 256 && p->N <= 256) {
+  if (enc && 2 * a.LX <= 256 && p->NZ <= 256) {
     if (p->tma_per_sm < 0) {
       p->tma_per_sm = p->kt->pass_b_tma_per_sm(a.LX, a.P1, a.P3);
       if (cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
@@ -724,9 +735,9 @@ void run_pass_b(xx_plan p, const PairArgs& a, cudaStream_t s) {
       }
     }
     if (p->tma_per_sm > 0) {
-      const cuuint64_t dims[3] = {(cuuint64_t)(2 * a.LX), (cuuint64_t)a.P2, (cuuint64_t)p->N * a.TA * a.TJ};
+      const cuuint64_t dims[3] = {(cuuint64_t)(2 * a.LX), (cuuint64_t)a.P2, (cuuint64_t)p->NZ * a.TA * a.TJ};
       const cuuint64_t strides[2] = {(cuuint64_t)a.LX * 8, (cuuint64_t)a.P2 * a.LX * 8};
-      const cuuint32_t box[3] = {(cuuint32_t)(2 * a.LX), 1, (cuuint32_t)p->N};
+      const cuuint32_t box[3] = {(cuuint32_t)(2 * a.LX), 1, (cuuint32_t)p->NZ};
       const cuuint32_t estr[3] = {1, 1, 1};
       CUtensorMap tm;
       if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.inter, dims, strides, box, estr,
@@ -1417,7 +1428,21 @@ int run_vjp_fused(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ,
   return XX_OK;
 }
 
-bool supported_grid(const int* g) { return g[0] == g[1] && g[1] == g[2] && supported_n(g[0]); }
+// Two equal axis lengths, each length built in; perm puts the equal pair first
+// (plan axes x, y), the third length on z.
+bool supported_grid(const int* g, int perm[3]) {
+  if (!supported_n(g[0]) || !supported_n(g[1]) || !supported_n(g[2])) return false;
+  if (g[0] == g[1]) {
+    perm[0] = 0, perm[1] = 1, perm[2] = 2;
+  } else if (g[0] == g[2]) {
+    perm[0] = 0, perm[1] = 2, perm[2] = 1;
+  } else if (g[1] == g[2]) {
+    perm[0] = 1, perm[1] = 2, perm[2] = 0;
+  } else {
+    return false;
+  }
+  return true;
+}
 
 }  // namespace
 
@@ -1458,7 +1483,28 @@ int xx_create(xx_plan* out, const double* lattice, const int* grid, int nk, cons
     if (!std::isfinite(kfrac[i])) return XX_ERR_INVALID_ARGUMENT;
   for (int k = 0; k < nk; ++k)
     if (npw[k] < 1 || npw[k] > npw_max) return XX_ERR_INVALID_ARGUMENT;
-  if (!supported_grid(grid)) return XX_ERR_UNSUPPORTED_GRID;
+  int perm[3];
+  if (!supported_grid(grid, perm)) return XX_ERR_UNSUPPORTED_GRID;
+  // Relabel the axes so that the two equal grid lengths are x and y: lattice
+  // rows, fractional k components and Miller components follow the grid.  The
+  // operator does not depend on the labelling; V_x c keeps the caller's basis
+  // order, and E_x and the Cartesian strain derivative are unchanged.
+  double lat[9];
+  int gridp[3];
+  for (int i = 0; i < 3; ++i) {
+    gridp[i] = grid[perm[i]];
+    for (int c = 0; c < 3; ++c) lat[3 * i + c] = lattice[3 * perm[i] + c];
+  }
+  std::vector<double> kfp(3 * (size_t)nk);
+  for (int k = 0; k < nk; ++k)
+    for (int i = 0; i < 3; ++i) kfp[3 * k + i] = kfrac[3 * k + perm[i]];
+  std::vector<int> milp(3 * (size_t)nk * npw_max);
+  for (size_t g = 0; g < (size_t)nk * npw_max; ++g)
+    for (int i = 0; i < 3; ++i) milp[3 * g + i] = miller[3 * g + perm[i]];
+  kfrac = kfp.data();
+  miller = milp.data();
+  grid = gridp;
+  lattice = lat;
 
   // cell volume and reciprocal metric (b_i = 2 pi inverse-transpose rows)
   const double* a = lattice;
@@ -1490,7 +1536,11 @@ int xx_create(xx_plan* out, const double* lattice, const int* grid, int nk, cons
   if (!p) return XX_ERR_OUT_OF_MEMORY;
   cudaGetDevice(&p->device);
   p->N = grid[0];
-  for (int i = 0; i < 3; ++i) p->grid[i] = grid[i];
+  p->NZ = grid[2];
+  for (int i = 0; i < 3; ++i) {
+    p->grid[i] = grid[i];
+    p->perm[i] = perm[i];
+  }
   p->nk = nk;
   p->npw_max = npw_max;
   std::memcpy(p->lattice, lattice, sizeof(p->lattice));
@@ -1529,27 +1579,50 @@ int xx_create(xx_plan* out, const double* lattice, const int* grid, int nk, cons
   p->mu = mu;
   p->prec = precision;
   p->cap = workspace_cap ? workspace_cap : kDefaultCap;
-  p->kt = kernel_table(p->N);
-
-  // twiddles exp(-2 pi i e / N), evaluated in long double on the host
-  std::vector<double2> t64(p->N);
-  std::vector<float2> t32(p->N);
-  for (int e = 0; e < p->N; ++e) {
-    const long double ang = -2.0L * 3.141592653589793238462643383279502884L * e / p->N;
-    t64[e] = make_double2((double)cosl(ang), (double)sinl(ang));
-    t32[e] = make_float2((float)t64[e].x, (float)t64[e].y);
+  // plane kernels (x, y) of length N, pencil kernels (z) of length NZ
+  p->kx = *kernel_table(p->N);
+  const KernelTable* tz = kernel_table(p->NZ);
+  for (KernelSet* ks : {&p->kx.f32, &p->kx.f64}) {
+    const KernelSet& zs = ks == &p->kx.f32 ? tz->f32 : tz->f64;
+    ks->pass_b = zs.pass_b;
+    ks->pass_b_dmu = zs.pass_b_dmu;
+    ks->pass_b_strain = zs.pass_b_strain;
+    ks->s2g_z = zs.s2g_z;
   }
+  p->kx.pass_b_tma = tz->pass_b_tma;
+  p->kx.pass_b_tma_per_sm = tz->pass_b_tma_per_sm;
+  p->kx.g2s_z = tz->g2s_z;
+  p->kt = &p->kx;
+
+  // twiddles exp(-2 pi i e / L) for L = N and NZ, evaluated in long double on the host
+  auto twiddles = [](int L, std::vector<double2>& t64, std::vector<float2>& t32) {
+    t64.resize(L);
+    t32.resize(L);
+    for (int e = 0; e < L; ++e) {
+      const long double ang = -2.0L * 3.141592653589793238462643383279502884L * e / L;
+      t64[e] = make_double2((double)cosl(ang), (double)sinl(ang));
+      t32[e] = make_float2((float)t64[e].x, (float)t64[e].y);
+    }
+  };
+  std::vector<double2> t64, tz64;
+  std::vector<float2> t32, tz32;
+  twiddles(p->N, t64, t32);
+  twiddles(p->NZ, tz64, tz32);
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc(&p->d_miller, sizeof(int) * 3 * (size_t)nk * npw_max);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_npw, sizeof(int) * nk);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_tw64, sizeof(double2) * p->N);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_tw32, sizeof(float2) * p->N);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_twz64, sizeof(double2) * p->NZ);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_twz32, sizeof(float2) * p->NZ);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_err, sizeof(int));
   if (e == cudaSuccess)
     e = cudaMemcpy(p->d_miller, miller, sizeof(int) * 3 * (size_t)nk * npw_max, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_npw, npw, sizeof(int) * nk, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_tw64, t64.data(), sizeof(double2) * p->N, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_tw32, t32.data(), sizeof(float2) * p->N, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_twz64, tz64.data(), sizeof(double2) * p->NZ, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_twz32, tz32.data(), sizeof(float2) * p->NZ, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1571,6 +1644,8 @@ int xx_destroy(xx_plan p) {
   if (p->d_npw) cudaFree(p->d_npw);
   if (p->d_tw32) cudaFree(p->d_tw32);
   if (p->d_tw64) cudaFree(p->d_tw64);
+  if (p->d_twz32) cudaFree(p->d_twz32);
+  if (p->d_twz64) cudaFree(p->d_twz64);
   if (p->d_err) cudaFree(p->d_err);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
@@ -1871,11 +1946,11 @@ int launch_batched(int pass, bool fp64, const std::vector<std::pair<const PairAr
     size_t smem = 0;
     for (size_t i = 0; i < count; ++i) {
       const PairArgs& a = *items[first + i].first;
-      const int n = items[first + i].second;
+      const int n = pass == kCellPassB ? a.nz : items[first + i].second;
       ci.item[i].a = a;
       ci.item[i].n = n;
       ci.item[i].cta0 = ctas;
-      ctas += cell_item_ctas(pass, a, n);
+      ctas += cell_item_ctas(pass, a);
       threads = std::max(threads, cell_body_threads(pass, fp64, n));
       smem = std::max(smem, cell_body_smem(pass, fp64, n, a.P1, a.P3));
     }
@@ -1897,7 +1972,8 @@ int xx_run_batched(int n_jobs, const xx_job* jobs, void* stream) {
   for (int i = 0; i < n_jobs; ++i) {
     const xx_job& j = jobs[i];
     xx_plan p = j.plan;
-    if (!p || p->prec != prec || p->nk != 1 || p->n_shards > 1 || !cell_length_supported(p->N))
+    if (!p || p->prec != prec || p->nk != 1 || p->n_shards > 1 || !cell_length_supported(p->N) ||
+        !cell_length_supported(p->NZ))
       return XX_ERR_INVALID_ARGUMENT;
     for (int k = 0; k < i; ++k)
       if (jobs[k].plan == p) return XX_ERR_INVALID_ARGUMENT;
@@ -1980,8 +2056,8 @@ int xx_run_batched(int n_jobs, const xx_job* jobs, void* stream) {
     }
     if (all.empty()) break;
     auto larger = [](const std::pair<const PairArgs*, int>& x, const std::pair<const PairArgs*, int>& y) {
-      const double wx = (double)x.second * x.second * x.second * x.first->TA * x.first->TJ;
-      const double wy = (double)y.second * y.second * y.second * y.first->TA * y.first->TJ;
+      const double wx = (double)x.second * x.second * x.first->nz * x.first->TA * x.first->TJ;
+      const double wy = (double)y.second * y.second * y.first->nz * y.first->TA * y.first->TJ;
       return wx > wy;
     };
     std::stable_sort(all.begin(), all.end(), larger);
@@ -2197,10 +2273,10 @@ int xx_exact_grid(const int* n_max, int* n_out) {
 int xx_plan_info(xx_plan p, xx_info* info) {
   if (!p || !info) return XX_ERR_INVALID_ARGUMENT;
   std::memset(info, 0, sizeof(*info));
-  for (int i = 0; i < 3; ++i) {
-    info->grid[i] = p->grid[i];
-    info->n_max[i] = p->nmax[i];
-    info->pruned[i] = 2 * p->h[i] + 1;
+  for (int i = 0; i < 3; ++i) {   // in the caller's axis order
+    info->grid[p->perm[i]] = p->grid[i];
+    info->n_max[p->perm[i]] = p->nmax[i];
+    info->pruned[p->perm[i]] = 2 * p->h[i] + 1;
   }
   info->nk = p->nk;
   info->npw_max = p->npw_max;

@@ -14,7 +14,8 @@ namespace xx {
 struct CellItem {
   PairArgs a;             // the batch, exactly as the single-cell passes take it
   long long cta0;         // first CTA of this item in the launch
-  int n;                  // FFT grid length of the cell
+  int n;                  // length of the pass's transforms: x, y (passes A, C and the
+                          // role-swapped C) or z (pass B) of the cell's grid
 };
 
 // Items of one launch; passed by value (kernel parameter space, < 32 KB).
@@ -28,15 +29,15 @@ static_assert(sizeof(CellItems) <= 32000, "kernel parameter space");
 enum CellPass { kCellPassA = 0, kCellPassB = 1, kCellPassC = 2, kCellPassCT = 3 };
 
 // CTAs of one item in a launch of the given pass.
-inline long long cell_item_ctas(int pass, const PairArgs& a, int n) {
+inline long long cell_item_ctas(int pass, const PairArgs& a) {
   switch (pass) {
     case kCellPassA:
     case kCellPassC:
-      return (long long)a.TA * n;
+      return (long long)a.TA * a.nz;
     case kCellPassB:
       return (long long)a.P2 * a.TA * a.TJ;
     default:
-      return (long long)a.TJ * n;
+      return (long long)a.TJ * a.nz;
   }
 }
 

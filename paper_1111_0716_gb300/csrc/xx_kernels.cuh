@@ -38,7 +38,9 @@ struct PairArgs {
   const double* w_tgt;   // [TA] occupations of the target batch
   const double2* w_pair; // [TJ] (w_2p, w_2p+1) of packed occupied slots (real orbitals)
   double* partial;       // [TA*TJ][P2] mu-gradient partial sums
-  const void* tw;        // [N] exp(-2 pi i e / N) in the pass precision
+  const void* tw;        // [N] exp(-2 pi i e / N) in the pass precision (x, y: plane passes)
+  const void* twz;       // [nz] exp(-2 pi i e / nz) (z: pencil passes)
+  int nz;                // z-planes of a grid (N3); the grid is N x N x nz
   long long u_tgt_stride;  // elements between consecutive target grids
   long long u_occ_stride;  // elements between consecutive occupied grids
   int TA, TJ;
@@ -67,7 +69,9 @@ struct GridArgs {        // sphere <-> grid
   void* stage;           // [nb][N][Q2][Q1]
   void* u;               // [nb][N^3] grids (sphere -> grid output)
   const double2* f;      // [nb][N^3] FP64 grids (grid -> sphere input)
-  const void* tw;
+  const void* tw;        // x, y twiddles (plane kernels)
+  const void* twz;       // z twiddles (pencil kernels)
+  int nz;                // z-planes of a grid (N3)
   int n1, n2, n3, Q1, Q2, Q3;
   double scale;
   int* err;
@@ -544,7 +548,7 @@ __device__ __forceinline__ void pass_a_body(const PairArgs& p, int ta, int z, un
   for (int tj = 0; tj < p.TJ; ++tj) {
     const C* uj = reinterpret_cast<const C*>(p.u_occ) + tj * p.u_occ_stride + z * plane;
     C* out = reinterpret_cast<C*>(p.inter) +
-             ((long long)(ta * p.TJ + tj) * N + z) * (long long)p.P2 * LX;
+             ((long long)(ta * p.TJ + tj) * p.nz + z) * (long long)p.P2 * LX;
     plane_forward<N, T, DB>(
         tw, s0, s1, p.h1, p.P1, p.h2,
         [&](int y, int x) { return cmulc(uj[y * N + x], ua[y * N + x]); },
@@ -565,7 +569,7 @@ __device__ __forceinline__ void pass_b_body(const PairArgs& p, int kyb, int pair
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* sZ = tw + N;
   C* sK = sZ + N * p.P1;
-  load_twiddles<N, T, NT>(tw, p.tw);
+  load_twiddles<N, T, NT>(tw, p.twz);
   bsync<NT>();
   const int P1 = p.P1, P2 = p.P2;
   const int zstride = P2 * p.LX;               // a pair's planes stay within 32-bit offsets
@@ -733,7 +737,7 @@ __global__ void __launch_bounds__(NT, 2) k_pass_b_tma(const __grid_constant__ CU
   C* buf0 = reinterpret_cast<C*>(smem_raw + pad);
   const int BUF = pass_b_tma_buf_elems<N>(LX);
   C* sK = buf0 + 2 * BUF;
-  const C* tw = reinterpret_cast<const C*>(p.tw);
+  const C* tw = reinterpret_cast<const C*>(p.twz);
   const unsigned bytes = (unsigned)(N * LX * sizeof(C));
   const int G = gridDim.x;
   const int zstride = P2 * LX;
@@ -832,7 +836,7 @@ __global__ void __launch_bounds__(PassASCfg<N>::NT, 1) k_pass_a_staged(PairArgs 
   st.start(uj0);
 #pragma unroll 1
   for (int tj = 0; tj < p.TJ; ++tj) {
-    C* out = reinterpret_cast<C*>(p.inter) + ((long long)(ta * p.TJ + tj) * N + z) * (long long)p.P2 * LX;
+    C* out = reinterpret_cast<C*>(p.inter) + ((long long)(ta * p.TJ + tj) * p.nz + z) * (long long)p.P2 * LX;
     const bool has_next = tj + 1 < p.TJ;
     const C* next = has_next ? uj0 + (tj + 1) * p.u_occ_stride : nullptr;
     if (!st.ready(tj)) return;
@@ -855,7 +859,7 @@ __global__ void __launch_bounds__(NT) k_pass_b_dmu(PairArgs p) {
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* sZ = tw + N;
   __shared__ double red[NT];
-  load_twiddles<N, T>(tw, p.tw);
+  load_twiddles<N, T>(tw, p.twz);
   __syncthreads();
   const int kyb = blockIdx.x, pair = blockIdx.y;
   const int P1 = p.P1, P2 = p.P2;
@@ -907,7 +911,7 @@ __device__ __forceinline__ void pass_c_body(const PairArgs& p, int ta, int z, un
 #pragma unroll 1
   for (int tj = 0; tj < p.TJ; ++tj) {
     const C* in = reinterpret_cast<const C*>(p.inter) +
-                  ((long long)(ta * p.TJ + tj) * N + z) * (long long)p.P2 * LX;
+                  ((long long)(ta * p.TJ + tj) * p.nz + z) * (long long)p.P2 * LX;
     const C* uj = reinterpret_cast<const C*>(p.u_occ) + tj * p.u_occ_stride + z * plane;
     T cf, cf2;
     if (PACKED) {
@@ -919,7 +923,7 @@ __device__ __forceinline__ void pass_c_body(const PairArgs& p, int ta, int z, un
       cf2 = (T)0;
     }
     const long long pbytes = (long long)p.P2 * LX * (long long)sizeof(C);
-    const C* next = tj + 1 < p.TJ ? in + (long long)N * p.P2 * LX : nullptr;
+    const C* next = tj + 1 < p.TJ ? in + (long long)p.nz * p.P2 * LX : nullptr;
     plane_inverse<N, T, false>(
         tw, tw2, s0, s1, p.h1, p.P1, p.h2, [&](int kyb, int kxb) { return in[kyb * LX + kxb]; },
         [&](int i, int k2, int y, int x, C v) {
@@ -934,7 +938,7 @@ __device__ __forceinline__ void pass_c_body(const PairArgs& p, int ta, int z, un
         },
         uj, plane * (long long)sizeof(C), next, pbytes);
   }
-  double2* dst = p.acc + ta * plane * N + z * plane;
+  double2* dst = p.acc + ta * plane * p.nz + z * plane;
 #pragma unroll
   for (int i = 0; i < G::X2_IT; ++i) {
     const int it = threadIdx.x + i * NT;
@@ -995,9 +999,9 @@ __device__ __forceinline__ void pass_ct_body(const PairArgs& p, int tj, int z, u
     for (int k2 = 0; k2 < B; ++k2) acc[i][k2] = czero<C>();
 #pragma unroll 1
   for (int ta = 0; ta < p.TA; ++ta) {
-    const C* in = reinterpret_cast<const C*>(p.inter) + ((long long)(ta * p.TJ + tj) * N + z) * pstride;
+    const C* in = reinterpret_cast<const C*>(p.inter) + ((long long)(ta * p.TJ + tj) * p.nz + z) * pstride;
     const C* fa = reinterpret_cast<const C*>(p.u_tgt) + ta * p.u_tgt_stride + z * plane;
-    const C* next = ta + 1 < p.TA ? in + (long long)p.TJ * N * pstride : nullptr;
+    const C* next = ta + 1 < p.TA ? in + (long long)p.TJ * p.nz * pstride : nullptr;
     const T wa = p.w_tgt ? (T)p.w_tgt[ta] : (T)1;
     plane_inverse<N, T, false>(
         tw, tw2, s0, s1, p.h1, p.P1, p.h2, [&](int kyb, int kxb) { return in[kyb * LX + kxb]; },
@@ -1009,7 +1013,7 @@ __device__ __forceinline__ void pass_ct_body(const PairArgs& p, int tj, int z, u
         fa, plane * (long long)sizeof(C), next, pstride * (long long)sizeof(C));
   }
   const double cf = p.coef * (p.w_occ ? p.w_occ[tj] : 1.0);
-  double2* dst = p.acc + tj * plane * N + z * plane;
+  double2* dst = p.acc + tj * plane * p.nz + z * plane;
 #pragma unroll
   for (int i = 0; i < G::X2_IT; ++i) {
     const int it = threadIdx.x + i * NT;
@@ -1129,7 +1133,7 @@ __global__ void __launch_bounds__(NT) k_pass_b_strain(PairArgs p) {
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* sZ = tw + N;
   __shared__ double red[7][NT];
-  load_twiddles<N, T>(tw, p.tw);
+  load_twiddles<N, T>(tw, p.twz);
   __syncthreads();
   const int kyb = blockIdx.x, pair = blockIdx.y;
   const int P1 = p.P1, P2 = p.P2;
@@ -1185,7 +1189,7 @@ __global__ void __launch_bounds__(NT) k_s2g_z(GridArgs g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* sZ = tw + N;
-  load_twiddles<N, T>(tw, g.tw);
+  load_twiddles<N, T>(tw, g.twz);
   __syncthreads();
   const int kyb = blockIdx.x, b = blockIdx.y;
   const int Q1 = g.Q1, Q2 = g.Q2, Q3 = g.Q3;
@@ -1196,7 +1200,7 @@ __global__ void __launch_bounds__(NT) k_s2g_z(GridArgs g) {
       [&](int z, int c, C v) { st[(long long)z * Q2 * Q1 + c] = v; });
 }
 
-// grid (nb, N): inverse y and x transforms of stage plane (b, z) into u[b][z]
+// grid (nb, nz): inverse y and x transforms of stage plane (b, z) into u[b][z]
 template <int N, typename T>
 __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_s2g_xy(GridArgs g) {
   using C = cplx<T>;
@@ -1212,15 +1216,15 @@ __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_s2g_xy(GridArgs g) {
   __syncthreads();
   const int b = blockIdx.x, z = blockIdx.y;
   const int Q1 = g.Q1, Q2 = g.Q2;
-  const C* st = reinterpret_cast<const C*>(g.stage) + ((long long)b * N + z) * Q2 * Q1;
-  C* u = reinterpret_cast<C*>(g.u) + (long long)b * N * N * N + (long long)z * N * N;
+  const C* st = reinterpret_cast<const C*>(g.stage) + ((long long)b * g.nz + z) * Q2 * Q1;
+  C* u = reinterpret_cast<C*>(g.u) + (long long)b * N * N * g.nz + (long long)z * N * N;
   const T sc = (T)g.scale;
   plane_inverse<N, T, true>(
       tw, tw2, s0, s1, g.n1, Q1, g.n2, [&](int kyb, int kxb) { return st[kyb * Q1 + kxb]; },
       [&](int, int, int y, int x, C v) { u[y * N + x] = sc * v; });
 }
 
-// grid (nb, N): forward x and y transforms of FP64 grid plane (b, z) into stage
+// grid (nb, nz): forward x and y transforms of FP64 grid plane (b, z) into stage
 template <int N>
 __global__ void __launch_bounds__(PlaneCfg<N, double>::NT) k_g2s_xy(GridArgs g) {
   using C = double2;
@@ -1233,8 +1237,8 @@ __global__ void __launch_bounds__(PlaneCfg<N, double>::NT) k_g2s_xy(GridArgs g) 
   __syncthreads();
   const int b = blockIdx.x, z = blockIdx.y;
   const int Q1 = g.Q1;
-  const C* f = g.f + (long long)b * N * N * N + (long long)z * N * N;
-  C* st = reinterpret_cast<C*>(g.stage) + ((long long)b * N + z) * g.Q2 * Q1;
+  const C* f = g.f + (long long)b * N * N * g.nz + (long long)z * N * N;
+  C* st = reinterpret_cast<C*>(g.stage) + ((long long)b * g.nz + z) * g.Q2 * Q1;
   plane_forward<N, double, PlaneCfg<N, double>::DB>(
       tw, s0, s1, g.n1, Q1, g.n2, [&](int y, int x) { return f[y * N + x]; },
       [&](int kyb, int kxb, C v) { st[kyb * Q1 + kxb] = v; });
@@ -1247,7 +1251,7 @@ __global__ void __launch_bounds__(NT) k_g2s_z(GridArgs g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* sZ = tw + N;
-  load_twiddles<N, double>(tw, g.tw);
+  load_twiddles<N, double>(tw, g.twz);
   __syncthreads();
   const int kyb = blockIdx.x, b = blockIdx.y;
   const int Q1 = g.Q1, Q2 = g.Q2, Q3 = g.Q3;

@@ -43,13 +43,13 @@ template <int N, typename T> void launch_pass_a(const PairArgs& p, cudaStream_t 
   if (sizeof(T) == 4 && p.stage_a) {
     const size_t sm = smem_pass_a_staged<N>();
     allow_smem(k_pass_a_staged<N>, sm);
-    k_pass_a_staged<N><<<dim3(p.TA, N), PassASCfg<N>::NT, sm, s>>>(p);
+    k_pass_a_staged<N><<<dim3(p.TA, p.nz), PassASCfg<N>::NT, sm, s>>>(p);
     return;
   }
   using G = PassACfg<N, T>;
   const size_t sm = G::smem();
   allow_smem(k_pass_a<N, T>, sm);
-  k_pass_a<N, T><<<dim3(p.TA, N), G::NT, sm, s>>>(p);
+  k_pass_a<N, T><<<dim3(p.TA, p.nz), G::NT, sm, s>>>(p);
 }
 template <int N, typename T> void launch_pass_b(const PairArgs& p, cudaStream_t s) {
   const size_t sm = smem_pencil<N, T>(p.P1, p.P3);
@@ -85,13 +85,13 @@ template <int N, typename T, bool PACKED> void launch_pass_c(const PairArgs& p, 
   using G = PlaneCfg<N, T>;
   const size_t sm = G::smem();
   allow_smem(k_pass_c<N, T, PACKED>, sm);
-  k_pass_c<N, T, PACKED><<<dim3(p.TA, N), G::NT, sm, s>>>(p);
+  k_pass_c<N, T, PACKED><<<dim3(p.TA, p.nz), G::NT, sm, s>>>(p);
 }
 template <int N, typename T> void launch_pass_ct(const PairArgs& p, cudaStream_t s) {
   using G = PlaneCfg<N, T>;
   const size_t sm = G::smem();
   allow_smem(k_pass_ct<N, T>, sm);
-  k_pass_ct<N, T><<<dim3(p.TJ, N), G::NT, sm, s>>>(p);
+  k_pass_ct<N, T><<<dim3(p.TJ, p.nz), G::NT, sm, s>>>(p);
 }
 template <int N, typename T> void launch_s2g_z(const GridArgs& g, cudaStream_t s) {
   const size_t sm = smem_pencil<N, T>(g.Q1, 0);
@@ -102,13 +102,13 @@ template <int N, typename T> void launch_s2g_xy(const GridArgs& g, cudaStream_t 
   using G = PlaneCfg<N, T>;
   const size_t sm = G::smem();
   allow_smem(k_s2g_xy<N, T>, sm);
-  k_s2g_xy<N, T><<<dim3(g.nb, N), G::NT, sm, s>>>(g);
+  k_s2g_xy<N, T><<<dim3(g.nb, g.nz), G::NT, sm, s>>>(g);
 }
 template <int N> void launch_g2s_xy(const GridArgs& g, cudaStream_t s) {
   using G = PlaneCfg<N, double>;
   const size_t sm = G::smem();
   allow_smem(k_g2s_xy<N>, sm);
-  k_g2s_xy<N><<<dim3(g.nb, N), G::NT, sm, s>>>(g);
+  k_g2s_xy<N><<<dim3(g.nb, g.nz), G::NT, sm, s>>>(g);
 }
 template <int N> void launch_g2s_z(const GridArgs& g, cudaStream_t s) {
   const size_t sm = smem_pencil<N, double>(g.Q1, 0);

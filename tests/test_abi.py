@@ -69,7 +69,8 @@ def _status(fn):
 def test_rejects_bad_arguments_before_gpu_work(lib):
     wl = synth.tiny_cubic()
     assert _status(lambda: _create(lib, wl, grid=(25, 25, 25))) == -2        # unsupported length
-    assert _status(lambda: _create(lib, wl, grid=(24, 24, 48))) == -2        # unequal axes
+    assert _status(lambda: _create(lib, wl, grid=(24, 32, 48))) == -2        # no two lengths equal
+    assert _status(lambda: _create(lib, wl, grid=(24, 25, 24))) == -2        # one length unsupported
     assert _status(lambda: _create(lib, wl, kernel=7)) == -1
     assert _status(lambda: _create(lib, wl, mu=0.0)) == -1                   # screened needs mu > 0
     assert _status(lambda: _create(lib, wl, mu=float("nan"))) == -1
