@@ -37,7 +37,7 @@
  * N_i >= 4 n_i + 1 where n_i is the largest |Miller index| along axis i over
  * all basis sets (the paper sizes its FFT grids so that no aliasing occurs);
  * otherwise xx_create returns XX_ERR_GRID_ALIASING.  Supported axis lengths:
- * 24, 32, 40, 48, 60, 64, 72, 80, 96, with at least two of the three equal
+ * 24, 32, 36, 40, 48, 54, 60, 64, 72, 80, 96, 108, with at least two of the three equal
  * (N x N x M in any axis order; the plan relabels the axes internally so the
  * equal pair spans its planes, which changes nothing in the results or in the
  * layout of any argument).  Three different lengths return
@@ -114,7 +114,10 @@ typedef struct {
  * batch of 64 targets x 80 occupied bands is halved (occupied first) until its
  * intermediate fits.  When a k-point has at most half as many occupied bands as
  * the batch is wide, the occupied sets of consecutive k-points share a batch.
- * Returns XX_ERR_INVALID_ARGUMENT, XX_ERR_UNSUPPORTED_GRID, XX_ERR_GRID_ALIASING,
+ * Returns XX_ERR_INVALID_ARGUMENT, XX_ERR_UNSUPPORTED_GRID (also when a row of
+ * z-planes of the pruned codensity does not fit one CTA's shared memory:
+ * (N3 + N3 P1 + P3 P1) complex values, P_i = 4 n_max,i + 1, in the plan's
+ * precision; e.g. FP64 with P1 = P3 = N3 = 96), XX_ERR_GRID_ALIASING,
  * XX_ERR_NO_DEVICE, XX_ERR_OUT_OF_MEMORY or XX_OK; *out is NULL on failure.
  */
 int xx_create(xx_plan *out, const double *lattice, const int *grid, int nk, const double *kfrac,

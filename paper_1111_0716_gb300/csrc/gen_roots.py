@@ -16,7 +16,7 @@ def _c(R, m):
 def _s(R, m):
     return float(mpmath.sin(2 * mpmath.pi * m / R))
 
-RADICES = (6, 9, 10, 12, 16)
+RADICES = (6, 9, 10, 12, 16, 18)
 
 
 def main():

@@ -30,25 +30,31 @@
 namespace xx {
 const KernelTable* kernel_table_24();
 const KernelTable* kernel_table_32();
+const KernelTable* kernel_table_36();
 const KernelTable* kernel_table_40();
 const KernelTable* kernel_table_48();
+const KernelTable* kernel_table_54();
 const KernelTable* kernel_table_60();
 const KernelTable* kernel_table_64();
 const KernelTable* kernel_table_72();
 const KernelTable* kernel_table_80();
 const KernelTable* kernel_table_96();
+const KernelTable* kernel_table_108();
 
 const KernelTable* kernel_table(int n) {
   switch (n) {
     case 24: return kernel_table_24();
     case 32: return kernel_table_32();
+    case 36: return kernel_table_36();
     case 40: return kernel_table_40();
     case 48: return kernel_table_48();
+    case 54: return kernel_table_54();
     case 60: return kernel_table_60();
     case 64: return kernel_table_64();
     case 72: return kernel_table_72();
     case 80: return kernel_table_80();
     case 96: return kernel_table_96();
+    case 108: return kernel_table_108();
     default: return nullptr;
   }
 }
@@ -1531,6 +1537,19 @@ int xx_create(xx_plan* out, const double* lattice, const int* grid, int nk, cons
     cudaGetLastError();
     return XX_ERR_NO_DEVICE;
   }
+  {
+    // the z pencils of pass B hold a row of z-planes (grid[2] x P1) and its kept
+    // frequencies (P3 x P1) in shared memory; the plane kernels fit by construction
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return XX_ERR_NO_DEVICE;
+    }
+    const long long P1 = 4 * nmax[0] + 1, P3 = 4 * nmax[2] + 1;
+    const long long pencil = (grid[2] + grid[2] * P1 + P3 * P1) * (precision == XX_FP64 ? 16 : 8);
+    if (pencil > optin) return XX_ERR_UNSUPPORTED_GRID;
+  }
 
   xx_plan p = new (std::nothrow) xx_plan_s();
   if (!p) return XX_ERR_OUT_OF_MEMORY;
@@ -2262,7 +2281,7 @@ int xx_exact_grid(const int* n_max, int* n_out) {
     const int m = 4 * n_max[ax] + 1;
     if (m > need) need = m;
   }
-  for (int n = need; n <= 96; ++n)
+  for (int n = need; n <= 108; ++n)
     if (supported_n(n)) {
       *n_out = n;
       return XX_OK;

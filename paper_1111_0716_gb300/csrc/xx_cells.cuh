@@ -41,7 +41,8 @@ inline long long cell_item_ctas(int pass, const PairArgs& a) {
   }
 }
 
-// Host side (xx_cells32.cu / xx_cells64.cu).
+// Host side (xx_cells32.cu / xx_cells64.cu).  Length 108 has no batched body: its
+// planes need more threads than the batched blocks hold.
 // Threads and dynamic shared memory of the body of `pass` for grid length n
 // (0 when n has no body); block size of a launch is the largest over its items.
 bool cell_length_supported(int n);
@@ -95,8 +96,10 @@ __global__ void __launch_bounds__(NTMAX, MINB) k_cells(const __grid_constant__ C
   switch (it.n) {
     case 24: cell_body<24, T, PASS>(it.a, l, smem_raw); break;
     case 32: cell_body<32, T, PASS>(it.a, l, smem_raw); break;
+    case 36: cell_body<36, T, PASS>(it.a, l, smem_raw); break;
     case 40: cell_body<40, T, PASS>(it.a, l, smem_raw); break;
     case 48: cell_body<48, T, PASS>(it.a, l, smem_raw); break;
+    case 54: cell_body<54, T, PASS>(it.a, l, smem_raw); break;
     case 60: cell_body<60, T, PASS>(it.a, l, smem_raw); break;
     case 64: cell_body<64, T, PASS>(it.a, l, smem_raw); break;
     case 72: cell_body<72, T, PASS>(it.a, l, smem_raw); break;

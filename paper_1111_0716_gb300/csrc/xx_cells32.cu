@@ -34,7 +34,7 @@ size_t body_smem(int pass, bool fp64, int P1, int P3) {
 
 bool cell_length_supported(int n) {
   switch (n) {
-    case 24: case 32: case 40: case 48: case 60: case 64: case 72: case 80: case 96:
+    case 24: case 32: case 36: case 40: case 48: case 54: case 60: case 64: case 72: case 80: case 96:
       return true;
     default:
       return false;
@@ -45,8 +45,10 @@ int cell_body_threads(int pass, bool fp64, int n) {
   switch (n) {
     case 24: return body_threads<24>(pass, fp64);
     case 32: return body_threads<32>(pass, fp64);
+    case 36: return body_threads<36>(pass, fp64);
     case 40: return body_threads<40>(pass, fp64);
     case 48: return body_threads<48>(pass, fp64);
+    case 54: return body_threads<54>(pass, fp64);
     case 60: return body_threads<60>(pass, fp64);
     case 64: return body_threads<64>(pass, fp64);
     case 72: return body_threads<72>(pass, fp64);
@@ -60,8 +62,10 @@ size_t cell_body_smem(int pass, bool fp64, int n, int P1, int P3) {
   switch (n) {
     case 24: return body_smem<24>(pass, fp64, P1, P3);
     case 32: return body_smem<32>(pass, fp64, P1, P3);
+    case 36: return body_smem<36>(pass, fp64, P1, P3);
     case 40: return body_smem<40>(pass, fp64, P1, P3);
     case 48: return body_smem<48>(pass, fp64, P1, P3);
+    case 54: return body_smem<54>(pass, fp64, P1, P3);
     case 60: return body_smem<60>(pass, fp64, P1, P3);
     case 64: return body_smem<64>(pass, fp64, P1, P3);
     case 72: return body_smem<72>(pass, fp64, P1, P3);

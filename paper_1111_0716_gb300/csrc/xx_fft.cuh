@@ -171,6 +171,8 @@ template <int R, bool INV, typename C> __device__ __forceinline__ void dft(C* x)
     dft_ct<4, 3, INV>(x);
   } else if constexpr (R == 16) {
     dft_ct<4, 4, INV>(x);
+  } else if constexpr (R == 18) {
+    dft_ct<2, 9, INV>(x);
   } else {
     static_assert(R == 0, "unsupported in-register DFT length");
   }
@@ -181,13 +183,16 @@ template <int R, bool INV, typename C> __device__ __forceinline__ void dft(C* x)
 template <int N> struct Fac;
 template <> struct Fac<24> { static constexpr int A = 8, B = 3; };
 template <> struct Fac<32> { static constexpr int A = 8, B = 4; };
+template <> struct Fac<36> { static constexpr int A = 6, B = 6; };
 template <> struct Fac<40> { static constexpr int A = 8, B = 5; };
 template <> struct Fac<48> { static constexpr int A = 8, B = 6; };
+template <> struct Fac<54> { static constexpr int A = 6, B = 9; };
 template <> struct Fac<60> { static constexpr int A = 6, B = 10; };
 template <> struct Fac<64> { static constexpr int A = 8, B = 8; };
 template <> struct Fac<72> { static constexpr int A = 8, B = 9; };
 template <> struct Fac<80> { static constexpr int A = 8, B = 10; };
 template <> struct Fac<96> { static constexpr int A = 8, B = 12; };
+template <> struct Fac<108> { static constexpr int A = 6, B = 18; };
 
 // inter-step twiddle: z * conj?(tw[(n2*k1) mod N]), tw[e] = exp(-2 pi i e / N)
 template <bool INV, typename C> __device__ __forceinline__ C tw_mul(C z, C w) {

@@ -94,8 +94,9 @@ struct VtabArgs {
 // transform's output and the y transform's data sit at natural positions
 // (row y, column x or f_x).  S and LD are chosen per N by csrc/bank_layout.py,
 // which counts the wavefronts of 8-byte accesses in half-warp phases over every
-// S in [B, B + 16] and LD in [N, N + 40]: the x steps replay 1.0x at N = 32, 96,
-// at most 1.2x at N = 24, 60, 72 and 1.5x at N = 40, 48, 64, 80.  The y steps
+// S in [B, B + 16] and LD in [N, N + 40]: the x steps replay 1.0x at N = 32, 36, 96,
+// at most 1.2x at N = 24, 60, 72, 1.34x at N = 108 and 1.5x at N = 40, 48, 54, 64, 80.
+// The y steps
 // (lanes over kept columns) are conflict-free when 16 divides N; otherwise the
 // wrap from column N - 1 to column 0 replays up to 2x in one half-warp.
 // FP32 planes use two buffers (the x-step exchange goes from one to the
@@ -105,13 +106,16 @@ struct VtabArgs {
 template <int N> struct Lay;
 template <> struct Lay<24> { static constexpr int A = 8, B = 3, S = 4, LD = 35; };
 template <> struct Lay<32> { static constexpr int A = 8, B = 4, S = 5, LD = 44; };
+template <> struct Lay<36> { static constexpr int A = 6, B = 6, S = 9, LD = 54; };
 template <> struct Lay<40> { static constexpr int A = 8, B = 5, S = 5, LD = 44; };
 template <> struct Lay<48> { static constexpr int A = 8, B = 6, S = 7, LD = 60; };
+template <> struct Lay<54> { static constexpr int A = 6, B = 9, S = 9, LD = 54; };
 template <> struct Lay<60> { static constexpr int A = 6, B = 10, S = 15, LD = 90; };
 template <> struct Lay<64> { static constexpr int A = 8, B = 8, S = 9, LD = 76; };
 template <> struct Lay<72> { static constexpr int A = 8, B = 9, S = 12, LD = 105; };
 template <> struct Lay<80> { static constexpr int A = 8, B = 10, S = 11, LD = 92; };
 template <> struct Lay<96> { static constexpr int A = 8, B = 12, S = 13, LD = 108; };
+template <> struct Lay<108> { static constexpr int A = 6, B = 18, S = 19, LD = 114; };
 
 constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
 constexpr int lcm_c(int a, int b) { return a / gcd_c(a, b) * b; }

@@ -114,9 +114,9 @@ def test_no_device_is_reported_without_a_gpu(lib):
 
 def test_exact_grid_is_the_smallest_admissible_supported_length(lib):
     """xx_exact_grid: the smallest supported N with N >= 4 n_max + 1 on every axis."""
-    supported = (24, 32, 40, 48, 60, 64, 72, 80, 96)
+    supported = (24, 32, 36, 40, 48, 54, 60, 64, 72, 80, 96, 108)
     for nm in [(0, 0, 0), (4, 4, 4), (5, 4, 4), (7, 7, 7), (7, 9, 8), (14, 14, 14), (14, 12, 13),
-               (15, 15, 15), (23, 1, 1)]:
+               (15, 15, 15), (23, 1, 1), (26, 1, 1)]:
         need = 4 * max(nm) + 1
         assert lib.xx_exact_grid(nm) == min(n for n in supported if n >= need)
     # the workloads' grids are admissible, and their smallest exact grids are smaller
@@ -124,7 +124,7 @@ def test_exact_grid_is_the_smallest_admissible_supported_length(lib):
         nm = wl.n_max()
         assert lib.xx_exact_grid(nm) == n
         assert wl.grid[0] >= 4 * nm.max() + 1
-    assert _status(lambda: lib.xx_exact_grid((24, 0, 0))) == -2
+    assert _status(lambda: lib.xx_exact_grid((27, 0, 0))) == -2
     assert _status(lambda: lib.xx_exact_grid((-1, 0, 0))) == -1
 
 

@@ -19,7 +19,7 @@ LAY = bl.lay_from_header()
 
 
 def test_every_supported_length_has_a_layout():
-    assert sorted(LAY) == [24, 32, 40, 48, 60, 64, 72, 80, 96]
+    assert sorted(LAY) == [24, 32, 36, 40, 48, 54, 60, 64, 72, 80, 96, 108]
     for N, (A, B, S, LD) in LAY.items():
         assert A * B == N and S >= B and LD >= max(N, (A - 1) * S + B)
 
@@ -41,11 +41,12 @@ def test_committed_layout_minimises_the_x_step_count(N):
 
 def test_x_step_replay_ratios():
     ratio = {N: (lambda c: c[0] / c[1])(bl.x_cost(N, *LAY[N])) for N in LAY}
-    for N in (32, 96):
+    for N in (32, 36, 96):
         assert ratio[N] == 1.0
     for N in (24, 60, 72):
         assert ratio[N] <= 1.2
-    for N in (40, 48, 64, 80):
+    assert ratio[108] <= 1.34
+    for N in (40, 48, 54, 64, 80):
         assert ratio[N] <= 1.5
 
 

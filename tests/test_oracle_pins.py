@@ -57,7 +57,7 @@ def test_fft_matches_direct_dft(oracle_mod, shape, sign):
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("n", [24, 32, 40, 48, 60, 64, 72, 80, 96])
+@pytest.mark.parametrize("n", [24, 32, 36, 40, 48, 54, 60, 64, 72, 80, 96, 108])
 def test_fft_matches_numpy_on_every_grid_length(oracle_mod, n):
     x = rand_c(np.random.default_rng(n), (3, 5, n))
     ref = np.fft.fftn(x)

@@ -30,7 +30,7 @@ def table():
 def test_every_root_is_the_rounded_unit_root():
     t = table()
     radices = sorted({R for _, R, _ in t})
-    assert radices == [6, 9, 10, 12, 16]
+    assert radices == [6, 9, 10, 12, 16, 18]
     for R in radices:
         for m in range(R):
             ang = 2.0 * math.pi * m / R
