@@ -127,7 +127,8 @@ def kernel_source_hash():
 
 
 def recorded_traffic(kernel, batch):
-    """DRAM bytes per launch from the committed ncu summary, or None when stale."""
+    """DRAM bytes per transformed band pair of a pass from the committed ncu summary,
+    or None when stale (other kernel sources or another batch shape)."""
     try:
         with open(TRAFFIC_FILE) as f:
             d = json.load(f)
@@ -135,7 +136,7 @@ def recorded_traffic(kernel, batch):
         return None
     if d.get("source_hash") != kernel_source_hash() or list(d.get("batch", [])) != list(batch):
         return None
-    return d.get("bytes_per_launch", {}).get(kernel)
+    return d.get("bytes_per_pair", {}).get(kernel)
 
 
 def batch_schedule(nk, n_occ, n_tgt, TA, TJ, G_max=1, sym=True, cross=True, owned=None):
@@ -657,7 +658,12 @@ def main():
     bytes_per_launch = model[dom] * args.steps / max(n_l, 1)
     achieved = bytes_per_launch / mean_s / 1e9 if mean_s > 0 else 0.0
     path_bytes = sum(model.values()) * args.steps
-    traffic = recorded_traffic(dom, [TA, TJ])
+    # DRAM bytes per launch from the recorded bytes per pair: the pairs the class's
+    # launches process (a mirrored batch's role-swapped pass C re-reads its pairs)
+    per_pair = recorded_traffic(dom, [TA, TJ])
+    class_pairs = sum(ta * tj * (2 if (dom == "pass_c" and kind == "mirrored") else 1)
+                      for kind, ta, tj in sched)
+    traffic = per_pair * class_pairs * args.steps / max(n_l, 1) if per_pair else None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "frac_kind": "model bytes (algorithmic) / time",
                 "peak_kind": peak_kind, "traffic": traffic,
