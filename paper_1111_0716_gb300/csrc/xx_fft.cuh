@@ -46,10 +46,14 @@ template <bool INV, typename C> __device__ __forceinline__ C rotq(C z) {
   return C{z.y, -z.x};
 }
 
-// z * exp(-+ 2 pi i m / R) with compile-time-foldable constants (m, R known after unrolling)
+// z * exp(-+ 2 pi i m / R) with compile-time-foldable constants (m, R known after unrolling);
+// the quarter turns are exact rotations and sign changes
 template <int R, bool INV, typename C> __device__ __forceinline__ C root_mul(C z, int m) {
   m %= R;
   if (m == 0) return z;
+  if (2 * m == R) return C{-z.x, -z.y};
+  if (4 * m == R) return rotq<INV>(z);
+  if (4 * m == 3 * R) return rotq<!INV>(z);
   using T = decltype(z.x);
   const T c = (T)xx_root_cos(R, m);
   const T s = INV ? (T)xx_root_sin(R, m) : -(T)xx_root_sin(R, m);
@@ -125,6 +129,43 @@ template <bool INV, typename C> __device__ __forceinline__ void dft8(C* x) {
 
 template <int R, bool INV, typename C> __device__ __forceinline__ void dft(C* x);
 
+constexpr int gcd_i(int a, int b) { return b == 0 ? a : gcd_i(b, a % b); }
+// inverse of a modulo m (a, m coprime), by search (m is a small radix)
+constexpr int modinv_i(int a, int m) {
+  int r = 1;
+  while ((a * r) % m != 1) ++r;
+  return r;
+}
+
+// Composite length R = P * Q with P, Q coprime, in registers, by the prime-factor
+// (Good-Thomas) mapping: input n = (Q n1 + P n2) mod R, output
+// k = (Q (Q^-1 mod P) k1 + P (P^-1 mod Q) k2) mod R turn the length-R DFT into a
+// P x Q two-dimensional DFT with no twiddle factors between the steps.
+template <int P, int Q, bool INV, typename C> __device__ __forceinline__ void dft_pfa(C* x) {
+  constexpr int R = P * Q;
+  static_assert(gcd_i(P, Q) == 1, "prime-factor mapping needs coprime factors");
+  constexpr int a = modinv_i(Q % P, P), b = modinv_i(P % Q, Q);
+  C y[R];
+#pragma unroll
+  for (int n2 = 0; n2 < Q; ++n2) {
+    C s[P];
+#pragma unroll
+    for (int n1 = 0; n1 < P; ++n1) s[n1] = x[(Q * n1 + P * n2) % R];
+    dft<P, INV>(s);
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) y[k1 * Q + n2] = s[k1];
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < P; ++k1) {
+    C s[Q];
+#pragma unroll
+    for (int n2 = 0; n2 < Q; ++n2) s[n2] = y[k1 * Q + n2];
+    dft<Q, INV>(s);
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) x[(Q * a * k1 + P * b * k2) % R] = s[k2];
+  }
+}
+
 // Composite length R = P * Q in registers (same two-step split as the lines).
 template <int P, int Q, bool INV, typename C> __device__ __forceinline__ void dft_ct(C* x) {
   constexpr int R = P * Q;
@@ -162,17 +203,17 @@ template <int R, bool INV, typename C> __device__ __forceinline__ void dft(C* x)
   } else if constexpr (R == 8) {
     dft8<INV>(x);
   } else if constexpr (R == 6) {
-    dft_ct<2, 3, INV>(x);
+    dft_pfa<2, 3, INV>(x);
   } else if constexpr (R == 9) {
     dft_ct<3, 3, INV>(x);
   } else if constexpr (R == 10) {
-    dft_ct<2, 5, INV>(x);
+    dft_pfa<2, 5, INV>(x);
   } else if constexpr (R == 12) {
-    dft_ct<4, 3, INV>(x);
+    dft_pfa<4, 3, INV>(x);
   } else if constexpr (R == 16) {
     dft_ct<4, 4, INV>(x);
   } else if constexpr (R == 18) {
-    dft_ct<2, 9, INV>(x);
+    dft_pfa<2, 9, INV>(x);
   } else {
     static_assert(R == 0, "unsupported in-register DFT length");
   }
@@ -198,6 +239,12 @@ template <> struct Fac<108> { static constexpr int A = 6, B = 18; };
 template <bool INV, typename C> __device__ __forceinline__ C tw_mul(C z, C w) {
   if (INV) return cmulc(w, z);
   return cmul(z, w);
+}
+// the same for output k1 of a first-step DFT: the twiddle of k1 = 0 is exactly 1
+// (k1 is a compile-time value after unrolling, so the multiply and the load fold away)
+template <bool INV, typename C> __device__ __forceinline__ C tw_mul(C z, C w, int k1) {
+  if (k1 == 0) return z;
+  return tw_mul<INV>(z, w);
 }
 
 // ----------------------------------------------------- frequency pruning --

@@ -214,7 +214,7 @@ __device__ __forceinline__ void plane_forward(const cplx<T>* tw, cplx<T>* s0, cp
       dft<A, false>(r);
 #pragma unroll
       for (int k1 = 0; k1 < A; ++k1)
-        s0[y * LD + k1 * S + n2] = tw_mul<false>(r[k1], G::REG_TW ? twr[k1] : tw[n2 * k1]);
+        s0[y * LD + k1 * S + n2] = tw_mul<false>(r[k1], G::REG_TW ? twr[k1] : tw[n2 * k1], k1);
     }
   }
   bsync<NT>();
@@ -269,7 +269,7 @@ __device__ __forceinline__ void plane_forward(const cplx<T>* tw, cplx<T>* s0, cp
       for (int n1 = 0; n1 < A; ++n1) r[n1] = sy[(B * n1 + n2) * LD + fx];
       dft<A, false>(r);
 #pragma unroll
-      for (int k1 = 0; k1 < A; ++k1) sy[(k1 * B + n2) * LD + fx] = tw_mul<false>(r[k1], tw[n2 * k1]);
+      for (int k1 = 0; k1 < A; ++k1) sy[(k1 * B + n2) * LD + fx] = tw_mul<false>(r[k1], tw[n2 * k1], k1);
     }
   }
   bsync<NT>();
@@ -333,7 +333,7 @@ __device__ __forceinline__ void plane_inverse(const cplx<T>* tw, const cplx<T>* 
       }
       dft<A, true>(r);
 #pragma unroll
-      for (int k1 = 0; k1 < A; ++k1) s0[(k1 * B + n2) * LD + xm] = tw_mul<true>(r[k1], tw[n2 * k1]);
+      for (int k1 = 0; k1 < A; ++k1) s0[(k1 * B + n2) * LD + xm] = tw_mul<true>(r[k1], tw[n2 * k1], k1);
     }
   }
   bsync<NT>();
@@ -372,7 +372,7 @@ __device__ __forceinline__ void plane_inverse(const cplx<T>* tw, const cplx<T>* 
         for (int k1 = 0; k1 < A; ++k1) {
           C w;
           if constexpr (REG) w = twr[k1]; else w = tw2[k1 * B + n2];
-          sx[row * LD + k1 * S + n2] = tw_mul<true>(r[k1], w);
+          sx[row * LD + k1 * S + n2] = tw_mul<true>(r[k1], w, k1);
         }
       }
     }
@@ -398,7 +398,7 @@ __device__ __forceinline__ void plane_inverse(const cplx<T>* tw, const cplx<T>* 
         for (int k1 = 0; k1 < A; ++k1) {
           C w;
           if constexpr (REG) w = twr[k1]; else w = tw2[k1 * B + n2];
-          sx[row * LD + k1 * S + n2] = tw_mul<true>(hold[k1], w);
+          sx[row * LD + k1 * S + n2] = tw_mul<true>(hold[k1], w, k1);
         }
       }
     }
@@ -447,7 +447,7 @@ __device__ __forceinline__ void pencil_forward(const cplx<T>* tw, cplx<T>* sZ, i
       for (int n1 = 0; n1 < A; ++n1) r[n1] = load(B * n1 + n2, c);
       dft<A, false>(r);
 #pragma unroll
-      for (int k1 = 0; k1 < A; ++k1) sZ[(k1 * B + n2) * ld + c] = tw_mul<false>(r[k1], tw[n2 * k1]);
+      for (int k1 = 0; k1 < A; ++k1) sZ[(k1 * B + n2) * ld + c] = tw_mul<false>(r[k1], tw[n2 * k1], k1);
     }
   }
   bsync<NT>();
@@ -490,7 +490,7 @@ __device__ __forceinline__ void pencil_inverse(const cplx<T>* tw, cplx<T>* sZ, i
       }
       dft<A, true>(r);
 #pragma unroll
-      for (int k1 = 0; k1 < A; ++k1) sZ[(k1 * B + n2) * ld + c] = tw_mul<true>(r[k1], tw[n2 * k1]);
+      for (int k1 = 0; k1 < A; ++k1) sZ[(k1 * B + n2) * ld + c] = tw_mul<true>(r[k1], tw[n2 * k1], k1);
     }
   }
   bsync<NT>();
