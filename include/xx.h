@@ -443,6 +443,15 @@ int xx_plan_info(xx_plan plan, xx_info *info);
 int xx_exact_grid(const int *n_max, int *n_out);
 
 /*
+ * The same per axis: the supported grid N1 x N2 x N3 with N_i >= 4 n_max,i + 1
+ * and two lengths equal (what xx_create accepts) that has the fewest points;
+ * grid_out[3] (host) in the caller's axis order.  Ties go to the first
+ * candidate in the order: axes (1, 2) equal, (1, 3) equal, (2, 3) equal.
+ * Host only.  Errors as xx_exact_grid.
+ */
+int xx_exact_grid3(const int *n_max, int *grid_out);
+
+/*
  * E_x reduction for callers that cannot allocate device memory.  The paper has
  * no counterpart: this entry point exists for callers whose device memory is
  * already reserved by their own memory manager (a framework's caching

@@ -1460,7 +1460,7 @@ const char* xx_status_string(int status) {
   switch (status) {
     case XX_OK: return "ok";
     case XX_ERR_INVALID_ARGUMENT: return "invalid argument";
-    case XX_ERR_UNSUPPORTED_GRID: return "unsupported FFT grid (equal axes of 24, 32, 40, 48, 60, 64, 72, 80 or 96)";
+    case XX_ERR_UNSUPPORTED_GRID: return "unsupported FFT grid (two equal axis lengths of 24, 32, 36, 40, 48, 54, 60, 64, 72, 80, 96 or 108; a z-pencil row within shared memory)";
     case XX_ERR_GRID_ALIASING: return "FFT grid too small: an axis has N < 4 n_max + 1 (codensity wrap-around)";
     case XX_ERR_OUT_OF_MEMORY: return "out of device memory";
     case XX_ERR_CUDA: return "CUDA error";
@@ -2287,6 +2287,31 @@ int xx_exact_grid(const int* n_max, int* n_out) {
       return XX_OK;
     }
   return XX_ERR_UNSUPPORTED_GRID;
+}
+
+int xx_exact_grid3(const int* n_max, int* grid_out) {
+  if (!n_max || !grid_out) return XX_ERR_INVALID_ARGUMENT;
+  int m[3];
+  for (int ax = 0; ax < 3; ++ax) {
+    if (n_max[ax] < 0 || n_max[ax] > 4096) return XX_ERR_INVALID_ARGUMENT;
+    const int nm1[3] = {n_max[ax], 0, 0};
+    const int st = xx_exact_grid(nm1, &m[ax]);
+    if (st != XX_OK) return st;
+  }
+  // the two axes made equal take the longer of their lengths
+  const int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+  long long best = -1;
+  for (const auto& pr : pairs) {
+    int g[3] = {m[0], m[1], m[2]};
+    const int L = std::max(m[pr[0]], m[pr[1]]);
+    g[pr[0]] = g[pr[1]] = L;
+    const long long pts = (long long)g[0] * g[1] * g[2];
+    if (best < 0 || pts < best) {
+      best = pts;
+      std::copy(g, g + 3, grid_out);
+    }
+  }
+  return XX_OK;
 }
 
 int xx_plan_info(xx_plan p, xx_info* info) {

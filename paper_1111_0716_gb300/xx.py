@@ -39,7 +39,7 @@ EXPORTS = ("xx_create", "xx_destroy", "xx_apply", "xx_apply_range", "xx_energy",
            "xx_profile_read", "xx_plan_info", "xx_status_string", "xx_exact_grid",
            "xx_energy_from_vx_noalloc", "xx_run_many", "xx_apply_vjp", "xx_set_option",
            "xx_strain_derivative", "xx_measure_fma_rate", "xx_set_shard", "xx_shard_blocks",
-           "xx_run_batched")
+           "xx_run_batched", "xx_exact_grid3")
 XX_OPT_PAIR_SYMMETRY = 0
 XX_OPT_REAL_GAMMA = 1
 XX_OPT_TMA_PASS_B = 2
@@ -111,6 +111,7 @@ def load(path: Optional[str] = None):
     lib.xx_strain_derivative.argtypes = [P, P, P, I, P, P, P]
     lib.xx_status_string.argtypes = [I]
     lib.xx_exact_grid.argtypes = [P, P]
+    lib.xx_exact_grid3.argtypes = [P, P]
     lib.xx_measure_fma_rate.argtypes = [I, P, P]
     lib.xx_set_shard.argtypes = [P, I, I]
     lib.xx_shard_blocks.argtypes = [I, I, I, I, P]
@@ -395,6 +396,14 @@ def xx_measure_fma_rate(precision: int, stream=None) -> float:
     _check(load().xx_measure_fma_rate(int(precision), _np_ptr(out), _stream_ptr(stream)),
            "xx_measure_fma_rate")
     return float(out[0])
+
+
+def xx_exact_grid3(n_max) -> tuple:
+    """Fewest-point supported grid (two lengths equal) with N_i >= 4 n_max,i + 1 per axis."""
+    nm = np.ascontiguousarray(np.asarray(n_max, dtype=np.int32).reshape(3))
+    out = np.zeros(3, dtype=np.int32)
+    _check(load().xx_exact_grid3(_np_ptr(nm), _np_ptr(out)), "xx_exact_grid3")
+    return tuple(int(v) for v in out)
 
 
 def xx_plan_info(plan) -> dict:

@@ -132,3 +132,21 @@ def test_binding_has_a_function_for_every_entry_point(lib):
     """The Python binding is thin: one function per C entry point, same name."""
     for n in declared_symbols():
         assert callable(getattr(lib, n, None)), n
+
+
+def test_exact_grid3_is_the_fewest_point_admissible_grid(lib):
+    """xx_exact_grid3 against a brute-force search over every supported grid with two
+    equal lengths (what xx_create accepts)."""
+    import itertools
+    supported = (24, 32, 36, 40, 48, 54, 60, 64, 72, 80, 96, 108)
+    for nm in [(0, 0, 0), (4, 4, 4), (7, 9, 8), (5, 5, 6), (14, 12, 13), (4, 9, 4), (9, 4, 4),
+               (22, 3, 3), (26, 1, 26)]:
+        need = [4 * v + 1 for v in nm]
+        cands = [g for g in itertools.product(supported, repeat=3)
+                 if all(g[i] >= need[i] for i in range(3))
+                 and (g[0] == g[1] or g[0] == g[2] or g[1] == g[2])]
+        best = min(g[0] * g[1] * g[2] for g in cands)
+        got = lib.xx_exact_grid3(nm)
+        assert got in cands and got[0] * got[1] * got[2] == best, (nm, got)
+    assert _status(lambda: lib.xx_exact_grid3((27, 0, 0))) == -2
+    assert _status(lambda: lib.xx_exact_grid3((0, -1, 0))) == -1
