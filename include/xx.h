@@ -37,11 +37,15 @@
  * N_i >= 4 n_i + 1 where n_i is the largest |Miller index| along axis i over
  * all basis sets (the paper sizes its FFT grids so that no aliasing occurs);
  * otherwise xx_create returns XX_ERR_GRID_ALIASING.  Supported axis lengths:
- * 24, 32, 36, 40, 48, 54, 60, 64, 72, 80, 96, 108, with at least two of the three equal
- * (N x N x M in any axis order; the plan relabels the axes internally so the
- * equal pair spans its planes, which changes nothing in the results or in the
- * layout of any argument).  Three different lengths return
- * XX_ERR_UNSUPPORTED_GRID.
+ * 24, 32, 36, 40, 48, 54, 60, 64, 72, 80, 96, 108 on each axis.  The transforms
+ * run on an N x N x M grid: with two lengths equal (any axis order) the plan
+ * relabels the axes internally so the equal pair spans its planes, which changes
+ * nothing in the results or in the layout of any argument.  With three different
+ * lengths the plan raises the shorter of two axes to the longer, choosing the
+ * pair that gives the fewest points; since the caller's grid is free of
+ * wrap-around, so is the raised one, and V_x c, E_x and the derivatives are those
+ * of the caller's grid up to rounding (the cost is that of the raised grid).
+ * xx_plan_info reports the grid the transforms run on.
  *
  * Ownership: the caller owns every input and output buffer (device memory
  * unless stated otherwise).  The plan owns its derived tables and workspace,
@@ -83,7 +87,7 @@ typedef struct xx_plan_s *xx_plan;
 
 /* Plan facts, filled by xx_plan_info. */
 typedef struct {
-  int grid[3];              /* FFT grid */
+  int grid[3];              /* FFT grid the transforms run on (caller's axis order) */
   int n_max[3];             /* largest |Miller index| per axis */
   int pruned[3];            /* kept codensity frequencies per axis, 4 n_max + 1 */
   int nk;                   /* k-points */
@@ -444,9 +448,11 @@ int xx_exact_grid(const int *n_max, int *n_out);
 
 /*
  * The same per axis: the supported grid N1 x N2 x N3 with N_i >= 4 n_max,i + 1
- * and two lengths equal (what xx_create accepts) that has the fewest points;
- * grid_out[3] (host) in the caller's axis order.  Ties go to the first
- * candidate in the order: axes (1, 2) equal, (1, 3) equal, (2, 3) equal.
+ * and two lengths equal (the shape the transforms run on) that has the fewest
+ * points; grid_out[3] (host) in the caller's axis order.  Ties go to the first
+ * candidate in the order: axes (1, 2) equal, (1, 3) equal, (2, 3) equal, as in
+ * xx_create's raising of three different lengths, so a plan created on the
+ * smallest admissible length per axis runs on this grid.
  * Host only.  Errors as xx_exact_grid.
  */
 int xx_exact_grid3(const int *n_max, int *grid_out);

@@ -1435,7 +1435,8 @@ int run_vjp_fused(xx_plan p, const void* c_occ, int ld_occ, const double* w_occ,
 }
 
 // Two equal axis lengths, each length built in; perm puts the equal pair first
-// (plan axes x, y), the third length on z.
+// (plan axes x, y), the third length on z.  Three different lengths are raised to
+// two equal ones in xx_create before this is asked.
 bool supported_grid(const int* g, int perm[3]) {
   if (!supported_n(g[0]) || !supported_n(g[1]) || !supported_n(g[2])) return false;
   if (g[0] == g[1]) {
@@ -1460,7 +1461,7 @@ const char* xx_status_string(int status) {
   switch (status) {
     case XX_OK: return "ok";
     case XX_ERR_INVALID_ARGUMENT: return "invalid argument";
-    case XX_ERR_UNSUPPORTED_GRID: return "unsupported FFT grid (two equal axis lengths of 24, 32, 36, 40, 48, 54, 60, 64, 72, 80, 96 or 108; a z-pencil row within shared memory)";
+    case XX_ERR_UNSUPPORTED_GRID: return "unsupported FFT grid (axis lengths 24, 32, 36, 40, 48, 54, 60, 64, 72, 80, 96 or 108; a z-pencil row within shared memory)";
     case XX_ERR_GRID_ALIASING: return "FFT grid too small: an axis has N < 4 n_max + 1 (codensity wrap-around)";
     case XX_ERR_OUT_OF_MEMORY: return "out of device memory";
     case XX_ERR_CUDA: return "CUDA error";
@@ -1489,6 +1490,40 @@ int xx_create(xx_plan* out, const double* lattice, const int* grid, int nk, cons
     if (!std::isfinite(kfrac[i])) return XX_ERR_INVALID_ARGUMENT;
   for (int k = 0; k < nk; ++k)
     if (npw[k] < 1 || npw[k] > npw_max) return XX_ERR_INVALID_ARGUMENT;
+  for (int ax = 0; ax < 3; ++ax)
+    if (!supported_n(grid[ax])) return XX_ERR_UNSUPPORTED_GRID;
+  // largest |Miller index| per axis of the caller's basis; the caller's grid must be
+  // free of wrap-around on every axis
+  int nmax[3] = {0, 0, 0};
+  for (int k = 0; k < nk; ++k)
+    for (int g = 0; g < npw[k]; ++g)
+      for (int ax = 0; ax < 3; ++ax) {
+        const int m = miller[((long long)k * npw_max + g) * 3 + ax];
+        const int am = m < 0 ? -m : m;
+        if (am > 4096) return XX_ERR_INVALID_ARGUMENT;
+        if (am > nmax[ax]) nmax[ax] = am;
+      }
+  for (int ax = 0; ax < 3; ++ax)
+    if (grid[ax] < 4 * nmax[ax] + 1) return XX_ERR_GRID_ALIASING;
+  // Three different lengths: compute on the grid that raises the shorter of two axes
+  // to the longer, the pair giving the fewest points.  The caller's grid is free of
+  // wrap-around (checked above), so the raised one is too, and both give the same
+  // V_x c, E_x and derivatives up to rounding.
+  int raised[3] = {grid[0], grid[1], grid[2]};
+  if (grid[0] != grid[1] && grid[0] != grid[2] && grid[1] != grid[2]) {
+    const int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    long long best = -1;
+    for (const auto& pr : pairs) {
+      int g[3] = {grid[0], grid[1], grid[2]};
+      g[pr[0]] = g[pr[1]] = std::max(grid[pr[0]], grid[pr[1]]);
+      const long long pts = (long long)g[0] * g[1] * g[2];
+      if (best < 0 || pts < best) {
+        best = pts;
+        std::copy(g, g + 3, raised);
+      }
+    }
+  }
+  grid = raised;
   int perm[3];
   if (!supported_grid(grid, perm)) return XX_ERR_UNSUPPORTED_GRID;
   // Relabel the axes so that the two equal grid lengths are x and y: lattice
@@ -1496,9 +1531,10 @@ int xx_create(xx_plan* out, const double* lattice, const int* grid, int nk, cons
   // operator does not depend on the labelling; V_x c keeps the caller's basis
   // order, and E_x and the Cartesian strain derivative are unchanged.
   double lat[9];
-  int gridp[3];
+  int gridp[3], nmaxp[3];
   for (int i = 0; i < 3; ++i) {
     gridp[i] = grid[perm[i]];
+    nmaxp[i] = nmax[perm[i]];
     for (int c = 0; c < 3; ++c) lat[3 * i + c] = lattice[3 * perm[i] + c];
   }
   std::vector<double> kfp(3 * (size_t)nk);
@@ -1511,6 +1547,7 @@ int xx_create(xx_plan* out, const double* lattice, const int* grid, int nk, cons
   miller = milp.data();
   grid = gridp;
   lattice = lat;
+  std::copy(nmaxp, nmaxp + 3, nmax);
 
   // cell volume and reciprocal metric (b_i = 2 pi inverse-transpose rows)
   const double* a = lattice;
@@ -1519,18 +1556,6 @@ int xx_create(xx_plan* out, const double* lattice, const int* grid, int nk, cons
   const double c12[3] = {a[1] * a[5] - a[2] * a[4], a[2] * a[3] - a[0] * a[5], a[0] * a[4] - a[1] * a[3]};
   const double vol = a[0] * c23[0] + a[1] * c23[1] + a[2] * c23[2];
   if (!(std::fabs(vol) > 1e-12)) return XX_ERR_INVALID_ARGUMENT;
-
-  int nmax[3] = {0, 0, 0};
-  for (int k = 0; k < nk; ++k)
-    for (int g = 0; g < npw[k]; ++g)
-      for (int ax = 0; ax < 3; ++ax) {
-        const int m = miller[((long long)k * npw_max + g) * 3 + ax];
-        const int am = m < 0 ? -m : m;
-        if (am > 4096) return XX_ERR_INVALID_ARGUMENT;
-        if (am > nmax[ax]) nmax[ax] = am;
-      }
-  for (int ax = 0; ax < 3; ++ax)
-    if (grid[ax] < 4 * nmax[ax] + 1) return XX_ERR_GRID_ALIASING;
 
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {

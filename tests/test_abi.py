@@ -69,7 +69,7 @@ def _status(fn):
 def test_rejects_bad_arguments_before_gpu_work(lib):
     wl = synth.tiny_cubic()
     assert _status(lambda: _create(lib, wl, grid=(25, 25, 25))) == -2        # unsupported length
-    assert _status(lambda: _create(lib, wl, grid=(24, 32, 48))) == -2        # no two lengths equal
+    assert _status(lambda: _create(lib, wl, grid=(24, 32, 50))) == -2        # one length unsupported
     assert _status(lambda: _create(lib, wl, grid=(24, 25, 24))) == -2        # one length unsupported
     assert _status(lambda: _create(lib, wl, kernel=7)) == -1
     assert _status(lambda: _create(lib, wl, mu=0.0)) == -1                   # screened needs mu > 0
@@ -91,6 +91,18 @@ def test_rejects_grids_with_codensity_wrap_around(lib):
     assert _status(lambda: _create(lib, wl6, grid=(24, 24, 24))) == -3
 
 
+def test_three_lengths_are_checked_on_the_callers_grid(lib):
+    """Three different lengths run on a raised grid (24 x 32 x 40 -> 24 x 40 x 40), but
+    wrap-around is judged on the caller's lengths: n_max = 8 along the second axis needs
+    33 points, so 32 there is rejected although the raised 40 would hold it."""
+    wl = synth.tiny_cubic()
+    mil = wl.miller.copy()
+    mil[0, 0, 1] = 8
+    bad = wl.replace(miller=mil)
+    assert _status(lambda: _create(lib, bad, grid=(24, 32, 40))) == -3
+    assert _status(lambda: _create(lib, bad, grid=(24, 36, 40))) != -3
+
+
 def test_null_plan_and_pointers(lib):
     L = lib.load()
     assert L.xx_apply(None, None, 0, None, 0, None, 0, None, None) == -1
@@ -110,6 +122,8 @@ def test_no_device_is_reported_without_a_gpu(lib):
         pytest.skip("a GPU is present")
     wl = synth.tiny_cubic()
     assert _status(lambda: _create(lib, wl)) == -8
+    # three different lengths pass the grid checks and reach the device query
+    assert _status(lambda: _create(lib, wl, grid=(24, 32, 48))) == -8
 
 
 def test_exact_grid_is_the_smallest_admissible_supported_length(lib):
@@ -136,7 +150,7 @@ def test_binding_has_a_function_for_every_entry_point(lib):
 
 def test_exact_grid3_is_the_fewest_point_admissible_grid(lib):
     """xx_exact_grid3 against a brute-force search over every supported grid with two
-    equal lengths (what xx_create accepts)."""
+    equal lengths (the shape the transforms run on)."""
     import itertools
     supported = (24, 32, 36, 40, 48, 54, 60, 64, 72, 80, 96, 108)
     for nm in [(0, 0, 0), (4, 4, 4), (7, 9, 8), (5, 5, 6), (14, 12, 13), (4, 9, 4), (9, 4, 4),

@@ -1,10 +1,12 @@
-"""FFT grids of different lengths per axis (two of the three equal; the plan
-relabels the axes so the equal pair spans its planes), against the FP64 oracle
-in both precisions: a tetragonal cell on N x N x M with a k-mesh (the pair
-symmetry across k-points), and sheared cells whose equal lengths are on axes
-(1, 3) and (2, 3), so both relabellings run.  The relabelling must not change
-results: the same cell passed with its axes already in the plan's order gives
-the same V_x c, E_x and strain derivative."""
+"""FFT grids of different lengths per axis, against the FP64 oracle in both
+precisions.  Two of the three equal: the plan relabels the axes so the equal pair
+spans its planes -- a tetragonal cell on N x N x M with a k-mesh (the pair symmetry
+across k-points), and sheared cells whose equal lengths are on axes (1, 3) and
+(2, 3), so both relabellings run.  Three different lengths: the plan runs on a
+grid raised to two equal lengths, and the oracle on the caller's grid -- an
+orthorhombic cell with a k-mesh and a sheared Gamma cell.  The relabelling must not
+change results: the same cell passed with its axes already in the plan's order
+gives the same V_x c, E_x and strain derivative."""
 import math
 
 import numpy as np
@@ -38,13 +40,30 @@ def sheared_23():
                                5, 5, [1.0] * 5, 73)
 
 
-CELLS = {"tetra": tetragonal, "sheared13": sheared_13, "sheared23": sheared_23}
+def orthorhombic():
+    # n_max = 5, 6, 8 per axis: 24 x 32 x 40 is admissible; raised to 24 x 40 x 40
+    return synth.make_workload("ortho-24x32x40", np.diag([10.0, 13.3, 16.6]), (24, 32, 40),
+                               synth.monkhorst_pack(2), math.pi, 4, 6, [1.0, 1.0, 0.75, 0.3], 74)
+
+
+def sheared_3lengths():
+    # raised to 36 x 48 x 36 (the pair (1, 3) gives the fewest points)
+    lat = np.array([[11.0, 0.0, 0.0], [1.3, 15.0, 0.0], [-0.6, 0.9, 13.0]])
+    return synth.make_workload("sheared-32x48x36", lat, (32, 48, 36), np.zeros((1, 3)), math.pi,
+                               5, 6, [1.0] * 4 + [0.5], 75)
+
+
+# cell -> the grid the transforms run on
+CELLS = {"tetra": (tetragonal, (24, 24, 32)), "sheared13": (sheared_13, (24, 32, 24)),
+         "sheared23": (sheared_23, (40, 24, 24)), "ortho": (orthorhombic, (24, 40, 40)),
+         "sheared3": (sheared_3lengths, (36, 48, 36))}
 
 
 @pytest.mark.parametrize("name", sorted(CELLS))
 @pytest.mark.parametrize("prec,tol", [(0, gu.FP32_TOL), (1, gu.FP64_TOL)])
 def test_anisotropic_grid_matches_oracle(gpu, oracle_mod, name, prec, tol):
-    wl = CELLS[name]()
+    make, runs_on = CELLS[name]
+    wl = make()
     assert np.all(4 * wl.n_max() + 1 <= np.array(wl.grid))
     ref = oracle_mod.apply(wl)
     e_ref, _ = oracle_mod.energy_from_vx(wl, ref)
@@ -53,7 +72,7 @@ def test_anisotropic_grid_matches_oracle(gpu, oracle_mod, name, prec, tol):
         w = "%s %s%s" % (name, "x".join(map(str, wl.grid)), " shared" if shared else "")
         assert gu.record(w, prec, "max|dVx|/max|Vx|", gu.rel_max(vx, ref), tol) <= tol
         assert gu.record(w, prec, "|dE_x|/|E_x|", gu.rel_err(e, e_ref), tol) <= tol
-        assert tuple(info["grid"]) == tuple(wl.grid)
+        assert tuple(info["grid"]) == runs_on
 
 
 def _relabelled(wl, perm):
@@ -68,7 +87,7 @@ def _relabelled(wl, perm):
 @pytest.mark.parametrize("name,perm", [("sheared13", (0, 2, 1)), ("sheared23", (1, 2, 0))])
 def test_relabelling_changes_nothing(gpu, name, perm):
     torch, xx = gpu
-    wl = CELLS[name]()
+    wl = CELLS[name][0]()
     same = _relabelled(wl, perm)          # already in the plan's order: no relabelling
     assert same.grid[0] == same.grid[1]
     out = []
