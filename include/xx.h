@@ -335,9 +335,10 @@ int xx_sync(xx_plan plan, void *stream, double timeout_s);
 #define XX_OPT_TMA_PASS_B 2     /* FP32 pass B (the z transforms and kernel multiply of the
                                    band-pair intermediates): 1 (default) runs the
                                    persistent kernel whose rows arrive by bulk tensor copies,
-                                   two rows ahead, when the kept f_x of a row are at most
-                                   3/4 of the grid length, else the one-row-per-block
-                                   kernel; 2 always the tensor-copy kernel; 0 never.  Both
+                                   two rows ahead, when the z length is at least 80 and the
+                                   kept f_x of a row are at most 3/4 of the x length, else
+                                   the one-row-per-block kernel; 2 always the tensor-copy
+                                   kernel; 0 never.  Both
                                    run the same arithmetic in the same order.  Other values
                                    give XX_ERR_INVALID_ARGUMENT. */
 
@@ -373,6 +374,13 @@ int xx_sync(xx_plan plan, void *stream, double timeout_s);
                                    it those calls use per-k accumulators (k = q symmetry only,
                                    VJP parts one after the other).  Negative values give
                                    XX_ERR_INVALID_ARGUMENT. */
+
+#define XX_OPT_TABLE_CACHE 7    /* value != 0 (default): the kernel tables v(k - q + G)/N of
+                                   every (k, q) are built in one launch at the first call that
+                                   needs them and kept for the plan's life, when they fit in
+                                   min(1 GiB, workspace_cap / 8) and nk^2 <= 65535; otherwise,
+                                   or with 0, each band-pair batch builds its tables.  The
+                                   values are the same either way.  0 frees the kept tables. */
 
 /* Set a plan option; XX_ERR_INVALID_ARGUMENT for an unknown option. */
 int xx_set_option(xx_plan plan, int option, long long value);

@@ -289,7 +289,7 @@ struct xx_plan_s {
   size_t cap = 0;
   int ta_user = 0, tj_user = 0;
   bool pair_symmetry = true;
-  int tma_pass_b = 1;          // XX_OPT_TMA_PASS_B: 0 off, 1 when pruning keeps <= 3/4 of a row, 2 always
+  int tma_pass_b = 1;          // XX_OPT_TMA_PASS_B: 0 off, 1 for z length >= 80 with <= 3/4 of a row kept, 2 always
   int stage_pass_a = 1;        // XX_OPT_STAGE_PASS_A: 0 off, 1 for N <= 64, 2 always
   bool test_wait_expiry = false;   // XX_OPT_TEST_WAIT_EXPIRY
   bool fused_vjp = true;           // XX_OPT_FUSED_VJP
@@ -319,7 +319,15 @@ struct xx_plan_s {
   void* d_twz64 = nullptr;
   int* d_err = nullptr;
   DevBuf u_tgt, u_occ, inter, acc, vt, dvt, box, stage, dots, partial, dmu_acc, vx_tmp, u_bar,
-      stab, cpack, wpair, acc2, cells_tab;
+      stab, cpack, wpair, acc2, cells_tab, vt_all, kf_dev;
+  // Kernel tables of every (k, q), built once (they depend only on the plan's
+  // cell, k-points and kernel) when they fit: vt_all_state 0 not built, 1 built
+  // (event vt_all_ev marks the end of the build), 2 built and known complete,
+  // -1 not used (too large).  vt_sel: the table segment the next band-pair batch
+  // reads (nullptr: the per-batch buffer vt).
+  int vt_all_state = 0;
+  cudaEvent_t vt_all_ev = nullptr;
+  const void* vt_sel = nullptr;
   size_t ws_bytes = 0, peak_bytes = 0;
   long long launches = 0;
   long long pairs = 0;          // band pairs (or packed slots) through pass A so far
@@ -338,6 +346,10 @@ namespace {
 
 const size_t kDefaultCap = (size_t)16 << 30;
 const int kDefaultTA = 64, kDefaultTJ = 80;   // band-pair batch (targets x occupied)
+// widest occupied batch when whole occupied sets of several q-points share one
+// (measured on GB300, alpha-boron cell, 18 occupied bands: 8 q-points per batch
+// 1.5 % faster than 4, 2 q-points 2.7 % slower)
+const int kDefaultTJMulti = 160;
 
 // NVTX range for timeline tools (nsys, ncu --nvtx); free when no tool is attached
 struct Range {
@@ -379,6 +391,12 @@ void release(DevBuf& b) {
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.bytes = 0;
+}
+
+// release a workspace buffer while the plan lives on (counted in ws_bytes)
+void release_counted(xx_plan p, DevBuf& b) {
+  p->ws_bytes -= b.bytes;
+  release(b);
 }
 
 bool supported_n(int n) { return kernel_table(n) != nullptr; }
@@ -522,11 +540,80 @@ int grid_to_sphere(xx_plan p, int k, const double2* f, int nb, double2* out, cud
   return XX_OK;
 }
 
+// The kernel tables of every (k, q) in one launch, when nk^2 tables fit in
+// min(1 GiB, workspace cap / 8) and nk^2 <= 65535 (the grid's y extent); the
+// values are those of the per-(k, q) launches (same device function).  A later
+// call on another stream waits for the build's event until it has completed.
+int build_all_tables(xx_plan p, cudaStream_t s) {
+  if (p->vt_all_state < 0) return XX_OK;
+  if (p->vt_all_state == 2) return XX_OK;
+  if (p->vt_all_state == 1) {
+    const cudaError_t q = cudaEventQuery(p->vt_all_ev);
+    if (q == cudaSuccess) {
+      p->vt_all_state = 2;
+      return XX_OK;
+    }
+    if (q != cudaErrorNotReady) return cuda_status(q);
+    cudaError_t e = cudaStreamWaitEvent(s, p->vt_all_ev, 0);
+    return e == cudaSuccess ? XX_OK : cuda_status(e);
+  }
+  const size_t eb = p->prec == XX_FP64 ? 8 : 4;
+  const long long nbox = (long long)P(p, 0) * P(p, 1) * P(p, 2);
+  const long long pairs = (long long)p->nk * p->nk;
+  const size_t bytes = (size_t)pairs * (size_t)nbox * eb;
+  const size_t limit = std::min((size_t)1 << 30, p->cap / 8);
+  if (pairs > 65535 || bytes > limit) {
+    p->vt_all_state = -1;
+    return XX_OK;
+  }
+  int st = ensure(p, p->kf_dev, (size_t)3 * p->nk * sizeof(double));
+  if (st) return st;
+  if ((st = ensure(p, p->vt_all, bytes))) return st;
+  cudaError_t e = cudaMemcpyAsync(p->kf_dev.p, p->kfrac.data(), (size_t)3 * p->nk * sizeof(double),
+                                  cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (!p->vt_all_ev && (e = cudaEventCreateWithFlags(&p->vt_all_ev, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_status(e);
+  VtabArgs a{};
+  std::memcpy(a.M, p->M, sizeof(a.M));
+  a.h1 = p->h[0];
+  a.h2 = p->h[1];
+  a.h3 = p->h[2];
+  a.P1 = P(p, 0);
+  a.P2 = P(p, 1);
+  a.P3 = P(p, 2);
+  a.kernel = p->kernel;
+  a.mu = p->mu;
+  a.inv_n = 1.0 / (double)n3(p);
+  a.inv_n2 = a.inv_n * a.inv_n;
+  const dim3 grid((unsigned)((nbox + 255) / 256), (unsigned)pairs);
+  const int ev = prof_begin(p, s);
+  if (p->prec == XX_FP64)
+    k_vtab_all<double><<<grid, 256, 0, s>>>((double*)p->vt_all.p, (const double*)p->kf_dev.p, p->nk, a);
+  else
+    k_vtab_all<float><<<grid, 256, 0, s>>>((float*)p->vt_all.p, (const double*)p->kf_dev.p, p->nk, a);
+  prof_end(p, XX_PROF_KERNEL_TABLE, ev, s);
+  if ((st = launched(p, 1))) return st;
+  if ((e = cudaEventRecord(p->vt_all_ev, s)) != cudaSuccess) return cuda_status(e);
+  p->vt_all_state = 1;
+  return XX_OK;
+}
+
 // v(k - q + G)/N (and dv/dmu/N^2) over the pruned box into table slot `slot` of
 // `slots` (each P1 P2 P3 values); the buffers are sized for every slot first
 int kernel_table_for(xx_plan p, int k, int q, bool with_dmu, cudaStream_t s, int slot = 0, int slots = 1) {
   const size_t eb = p->prec == XX_FP64 ? 8 : 4;
   const long long nbox = (long long)P(p, 0) * P(p, 1) * P(p, 2);
+  p->vt_sel = nullptr;
+  if (!with_dmu) {
+    const int st = build_all_tables(p, s);
+    if (st) return st;
+    if (p->vt_all_state > 0) {
+      // consecutive q of one segment are consecutive tables
+      p->vt_sel = (const char*)p->vt_all.p + ((long long)k * p->nk + q - slot) * nbox * (long long)eb;
+      return XX_OK;
+    }
+  }
   int st = ensure(p, p->vt, (size_t)slots * nbox * eb);
   if (st) return st;
   if (with_dmu && (st = ensure(p, p->dvt, (size_t)slots * nbox * eb))) return st;
@@ -573,7 +660,7 @@ void batch_shape(xx_plan p, int n_tgt, int n_occ, int* TA, int* TJ) {
 PairArgs pair_args(xx_plan p, int TA, int TJ) {
   PairArgs a{};
   a.inter = p->inter.p;
-  a.vt = p->vt.p;
+  a.vt = p->vt_sel ? p->vt_sel : p->vt.p;
   a.dvt = p->dvt.p;
   a.partial = (double*)p->partial.p;
   a.tw = p->prec == XX_FP64 ? p->d_tw64 : p->d_tw32;
@@ -730,7 +817,10 @@ void run_pass_b(xx_plan p, const PairArgs& a, cudaStream_t s) {
   // measured on GB300 (beta cell, 64 targets x 160 occupied x 8 q): P1 = 57 of N = 96,
   // tensor-copy kernel 6.7 % faster than the row kernel (243.9 vs 261.3 ms); P1 = 57
   // of N = 60, 14 % slower
-  const bool want = p->tma_pass_b == 2 || (p->tma_pass_b == 1 && 4 * a.P1 <= 3 * p->N);
+  // measured on GB300 (cubic cells, 2x2x2 k-mesh, 32 x 32 bands; the beta cell): the
+  // tensor-copy kernel gains 6-7 % of pass B at N = 80 and 96 with P1 = 57 and is
+  // within 4 % either way at N = 96 otherwise, but loses 3-28 % at N <= 72
+  const bool want = p->tma_pass_b == 2 || (p->tma_pass_b == 1 && p->NZ >= 80 && 4 * a.P1 <= 3 * p->N);
   PFN_cuTensorMapEncodeTiled_v12000 enc = p->prec == XX_FP32_MIXED && want ? tensor_map_encoder() : nullptr;
   if (enc && 2 * a.LX <= 256 && p->NZ <= 256) {
     if (p->tma_per_sm < 0) {
@@ -832,7 +922,7 @@ int run_apply(xx_plan p, int k0, int kn, const void* c_occ, int ld_occ, const do
   // An occupied batch spans G_max consecutive q-points when a q-point's whole
   // occupied set fits the batch width at least twice (few bands, many k-points):
   // fewer, wider launches.
-  const int tj_cap = p->tj_user > 0 ? p->tj_user : kDefaultTJ;
+  const int tj_cap = p->tj_user > 0 ? p->tj_user : kDefaultTJMulti;
   int G_max = 1;
   if (n_occ > 0 && 2 * n_occ <= tj_cap) {
     G_max = tj_cap / n_occ < p->nk ? tj_cap / n_occ : p->nk;
@@ -1682,8 +1772,9 @@ int xx_destroy(xx_plan p) {
   cudaDeviceSynchronize();
   DevBuf* bufs[] = {&p->u_tgt, &p->u_occ, &p->inter, &p->acc, &p->vt, &p->dvt, &p->box,
                     &p->stage, &p->dots, &p->partial, &p->dmu_acc, &p->vx_tmp, &p->u_bar,
-                    &p->stab, &p->cpack, &p->wpair, &p->acc2, &p->cells_tab};
+                    &p->stab, &p->cpack, &p->wpair, &p->acc2, &p->cells_tab, &p->vt_all, &p->kf_dev};
   for (DevBuf* b : bufs) release(*b);
+  if (p->vt_all_ev) cudaEventDestroy(p->vt_all_ev);
   if (p->d_miller) cudaFree(p->d_miller);
   if (p->d_npw) cudaFree(p->d_npw);
   if (p->d_tw32) cudaFree(p->d_tw32);
@@ -2241,6 +2332,15 @@ int xx_set_option(xx_plan p, int option, long long value) {
     case XX_OPT_TMA_PASS_B:
       if (value < 0 || value > 2) return XX_ERR_INVALID_ARGUMENT;
       p->tma_pass_b = (int)value;
+      return XX_OK;
+    case XX_OPT_TABLE_CACHE:
+      if (value == 0) {
+        release_counted(p, p->vt_all);
+        p->vt_all_state = -1;
+      } else if (p->vt_all_state < 0) {
+        p->vt_all_state = 0;
+      }
+      p->vt_sel = nullptr;
       return XX_OK;
     default:
       return XX_ERR_INVALID_ARGUMENT;

@@ -1045,31 +1045,57 @@ __global__ void __launch_bounds__(PlaneCfg<N, T>::NT) k_pass_ct(PairArgs p) {
 // ------------------------------------------------------ kernel table (a2) --
 
 // v(k - q + G)/N and dv/dmu/N^2 over the pruned box, evaluated in FP64.
+// v(g)/N (and dv/dmu/N^2) at box index i of the pruned box, g = k - q + G with
+// d = k - q (fractional)
+__device__ __forceinline__ void vtab_value(const VtabArgs& a, const double d[3], long long i, double& v,
+                                           double& dv) {
+  const int kx = (int)(i % a.P1), ky = (int)((i / a.P1) % a.P2), kz = (int)(i / ((long long)a.P1 * a.P2));
+  const double m0 = (double)(kx - a.h1) + d[0];
+  const double m1 = (double)(ky - a.h2) + d[1];
+  const double m2 = (double)(kz - a.h3) + d[2];
+  const bool zero = (m0 == 0.0 && m1 == 0.0 && m2 == 0.0);
+  const double g2 = m0 * (a.M[0] * m0 + a.M[1] * m1 + a.M[2] * m2) +
+                    m1 * (a.M[3] * m0 + a.M[4] * m1 + a.M[5] * m2) +
+                    m2 * (a.M[6] * m0 + a.M[7] * m1 + a.M[8] * m2);
+  const double pi = 3.14159265358979323846;
+  if (a.kernel == 0) {
+    const double x = g2 / (4.0 * a.mu * a.mu);
+    v = zero ? pi / (a.mu * a.mu) : 4.0 * pi / g2 * (-expm1(-x));
+    dv = -2.0 * pi / (a.mu * a.mu * a.mu) * exp(-x);
+  } else {
+    v = zero ? 0.0 : 4.0 * pi / g2;
+    dv = 0.0;
+  }
+  v *= a.inv_n;
+  dv *= a.inv_n2;
+}
+
 template <typename T>
 __global__ void k_vtab(T* vt, T* dvt, VtabArgs a) {
   const long long n = (long long)a.P1 * a.P2 * a.P3;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int kx = (int)(i % a.P1), ky = (int)((i / a.P1) % a.P2), kz = (int)(i / ((long long)a.P1 * a.P2));
-    const double m0 = (double)(kx - a.h1) + a.d[0];
-    const double m1 = (double)(ky - a.h2) + a.d[1];
-    const double m2 = (double)(kz - a.h3) + a.d[2];
-    const bool zero = (m0 == 0.0 && m1 == 0.0 && m2 == 0.0);
-    const double g2 = m0 * (a.M[0] * m0 + a.M[1] * m1 + a.M[2] * m2) +
-                      m1 * (a.M[3] * m0 + a.M[4] * m1 + a.M[5] * m2) +
-                      m2 * (a.M[6] * m0 + a.M[7] * m1 + a.M[8] * m2);
-    const double pi = 3.14159265358979323846;
     double v, dv;
-    if (a.kernel == 0) {
-      const double x = g2 / (4.0 * a.mu * a.mu);
-      v = zero ? pi / (a.mu * a.mu) : 4.0 * pi / g2 * (-expm1(-x));
-      dv = -2.0 * pi / (a.mu * a.mu * a.mu) * exp(-x);
-    } else {
-      v = zero ? 0.0 : 4.0 * pi / g2;
-      dv = 0.0;
-    }
-    vt[i] = (T)(v * a.inv_n);
-    if (dvt) dvt[i] = (T)(dv * a.inv_n2);
+    vtab_value(a, a.d, i, v, dv);
+    vt[i] = (T)v;
+    if (dvt) dvt[i] = (T)dv;
+  }
+}
+
+// Every (k, q) table at once: blockIdx.y = k * nk + q, table (k, q) at
+// vt + (k * nk + q) * box (kfrac: [nk][3] fractional k-points).
+template <typename T>
+__global__ void k_vtab_all(T* vt, const double* kfrac, int nk, VtabArgs a) {
+  const long long n = (long long)a.P1 * a.P2 * a.P3;
+  const int k = blockIdx.y / nk, q = blockIdx.y % nk;
+  const double d[3] = {kfrac[3 * k] - kfrac[3 * q], kfrac[3 * k + 1] - kfrac[3 * q + 1],
+                       kfrac[3 * k + 2] - kfrac[3 * q + 2]};
+  T* out = vt + (long long)blockIdx.y * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v, dv;
+    vtab_value(a, d, i, v, dv);
+    out[i] = (T)v;
   }
 }
 

@@ -47,6 +47,7 @@ XX_OPT_STAGE_PASS_A = 3
 XX_OPT_TEST_WAIT_EXPIRY = 4
 XX_OPT_FUSED_VJP = 5
 XX_OPT_ACC_LIMIT_MB = 6
+XX_OPT_TABLE_CACHE = 7
 
 PROF_CLASSES = ("pass_a", "pass_b", "pass_c", "sphere_to_grid", "grid_to_sphere",
                 "kernel_table", "reduce", "pass_b_dmu")
@@ -464,6 +465,10 @@ class Plan:
     def set_tma_pass_b(self, mode: int):
         """0: one-row-per-block pass B; 1: automatic (default); 2: tensor-copy kernel."""
         xx_set_option(self.handle, XX_OPT_TMA_PASS_B, int(mode))
+
+    def set_table_cache(self, enable: bool):
+        """Keep the kernel tables of every (k, q) (default) or build them per batch."""
+        xx_set_option(self.handle, XX_OPT_TABLE_CACHE, 1 if enable else 0)
 
     def set_stage_pass_a(self, mode: int):
         """0: two CTAs per SM with global loads; 1: automatic (default); 2: staged."""

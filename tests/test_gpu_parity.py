@@ -332,6 +332,38 @@ def test_accumulator_limit_falls_back_to_per_k_accumulators(gpu):
     plan.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_kept_kernel_tables_change_nothing(gpu, prec):
+    """The kernel tables of every (k, q), built once and kept (XX_OPT_TABLE_CACHE,
+    default), against tables built per band-pair batch: the same values, so the
+    same V_x c and E_x bit for bit, with one table launch per plan instead of one
+    per (k, q) and batch; the apply and the backward (which builds its dv/dmu
+    tables per batch) still agree after the option is switched back and forth."""
+    torch, xx = gpu
+    wl = rhombo24()
+    out = []
+    for cache in (True, False, True):
+        plan = xx.Plan.from_workload(wl, precision=prec)
+        plan.set_batch(3, 3)
+        plan.set_table_cache(cache)
+        c = gu.dev(wl.c_tgt)
+        plan.profile(True)
+        ex, vx = plan.energy(c, gu.dev(wl.w_occ), c, gu.dev(wl.w_tgt), shared=True)
+        tables = plan.profile_read(reset=True)["kernel_table"][1]
+        dc, dmu = plan.backward(c, gu.dev(wl.w_tgt))
+        ex2, vx2 = plan.energy(c, gu.dev(wl.w_occ), c, gu.dev(wl.w_tgt), shared=True)
+        plan.sync(timeout_s=600.0)
+        out.append((vx.cpu().numpy(), ex.cpu().numpy(), vx2.cpu().numpy(), dc.cpu().numpy(),
+                    float(dmu.item()), tables))
+        plan.close()
+    for o in out[1:]:
+        assert np.array_equal(o[0], out[0][0]) and np.array_equal(o[1], out[0][1])
+        assert np.array_equal(o[2], out[0][0]) and np.array_equal(o[3], out[0][3])
+        assert o[4] == out[0][4]
+    assert out[0][5] == 1 and out[2][5] == 1
+    assert out[1][5] > wl.nk
+
+
 @pytest.mark.parametrize("prec,tol", [(0, gu.FP32_TOL), (1, gu.FP64_TOL)])
 def test_grid_64_k_mesh(gpu, oracle_mod, prec, tol):
     """The one supported FFT length no other workload uses (64 = 8 x 8): a cubic
@@ -354,7 +386,7 @@ def test_grid_64_k_mesh(gpu, oracle_mod, prec, tol):
 @pytest.mark.parametrize("shared", [True, False])
 def test_q_point_segments_match_single_q_batches(gpu, shared):
     """Occupied sets of several k-points in one batch (default: 4 bands per k-point
-    and a batch 80 wide) against one k-point per batch (occupied width 4), FP64,
+    and a batch up to 160 wide) against one k-point per batch (occupied width 4), FP64,
     with the pair symmetry (shared grids, split layout) and without (separate
     occupied array)."""
     torch, xx = gpu
