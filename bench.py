@@ -114,12 +114,15 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_beta_boron_96.json")
 
 
 def kernel_source_hash():
-    """Hash of the device-code sources (the kernels, their FFT building blocks and
-    launchers; not the host loops of xx_api.cu): recorded DRAM traffic per launch
-    is only valid for these kernels."""
+    """Hash of the sources of the single-cell kernels (the passes, their FFT building
+    blocks and launchers, and the per-length translation units; not the host loops of
+    xx_api.cu nor the batched multi-cell kernels): recorded DRAM traffic per launch is
+    only valid for these kernels."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1111_0716_gb300", "csrc")
-    files = glob.glob(os.path.join(csrc, "*.cuh")) + glob.glob(os.path.join(csrc, "xx_n*.cu"))
+    files = [os.path.join(csrc, f) for f in ("xx_launch.cuh", "xx_kernels.cuh", "xx_fft.cuh",
+                                             "xx_roots.cuh")] + \
+        glob.glob(os.path.join(csrc, "xx_n*.cu"))
     for f in sorted(files):
         with open(f, "rb") as fh:
             h.update(fh.read())
@@ -331,6 +334,10 @@ def profile_case(args):
         return
     plan = xx.Plan.from_workload(wl, precision=prec)
     nt, no = (16, 16) if args.profile_small else (64, 80)
+    if args.profile_small:
+        # the bench's occupied width: 80 columns (the whole sets of 5 q-points), so the
+        # FP64 accumulator update is spread over as many pairs as in the bench
+        plan.set_batch(16, 80)
     co = torch.from_numpy(wl.c_occ[:, :no].copy()).cuda()
     wo = torch.from_numpy(wl.w_occ[:, :no].copy()).cuda()
     ct = torch.from_numpy(wl.c_tgt[:1, :nt].copy()).cuda()

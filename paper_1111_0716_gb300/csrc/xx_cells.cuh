@@ -86,6 +86,20 @@ __device__ __forceinline__ void cell_body(const PairArgs& a, long long l, unsign
   }
 }
 
+// Threads of a body (what cell_body_threads reports on the host).
+template <int N, typename T, int PASS> __host__ __device__ constexpr int cell_body_nt() {
+  if constexpr (PASS == kCellPassB) return 256;
+  else if constexpr (PASS == kCellPassA) return PlaneCfg<N, T, cell_pass_a_db<N, T>()>::NT;
+  else return PlaneCfg<N, T>::NT;
+}
+
+// A body is compiled into a kernel only when its threads fit the kernel's
+// block bound; the host picks a kernel whose bound covers every item's body.
+template <int N, typename T, int PASS, int NTMAX>
+__device__ __forceinline__ void cell_body_fit(const PairArgs& a, long long l, unsigned char* smem) {
+  if constexpr (cell_body_nt<N, T, PASS>() <= NTMAX) cell_body<N, T, PASS>(a, l, smem);
+}
+
 template <typename T, int PASS, int NTMAX, int MINB>
 __global__ void __launch_bounds__(NTMAX, MINB) k_cells(const __grid_constant__ CellItems items) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -94,17 +108,17 @@ __global__ void __launch_bounds__(NTMAX, MINB) k_cells(const __grid_constant__ C
   const CellItem& it = items.item[i];
   const long long l = b - it.cta0;
   switch (it.n) {
-    case 24: cell_body<24, T, PASS>(it.a, l, smem_raw); break;
-    case 32: cell_body<32, T, PASS>(it.a, l, smem_raw); break;
-    case 36: cell_body<36, T, PASS>(it.a, l, smem_raw); break;
-    case 40: cell_body<40, T, PASS>(it.a, l, smem_raw); break;
-    case 48: cell_body<48, T, PASS>(it.a, l, smem_raw); break;
-    case 54: cell_body<54, T, PASS>(it.a, l, smem_raw); break;
-    case 60: cell_body<60, T, PASS>(it.a, l, smem_raw); break;
-    case 64: cell_body<64, T, PASS>(it.a, l, smem_raw); break;
-    case 72: cell_body<72, T, PASS>(it.a, l, smem_raw); break;
-    case 80: cell_body<80, T, PASS>(it.a, l, smem_raw); break;
-    case 96: cell_body<96, T, PASS>(it.a, l, smem_raw); break;
+    case 24: cell_body_fit<24, T, PASS, NTMAX>(it.a, l, smem_raw); break;
+    case 32: cell_body_fit<32, T, PASS, NTMAX>(it.a, l, smem_raw); break;
+    case 36: cell_body_fit<36, T, PASS, NTMAX>(it.a, l, smem_raw); break;
+    case 40: cell_body_fit<40, T, PASS, NTMAX>(it.a, l, smem_raw); break;
+    case 48: cell_body_fit<48, T, PASS, NTMAX>(it.a, l, smem_raw); break;
+    case 54: cell_body_fit<54, T, PASS, NTMAX>(it.a, l, smem_raw); break;
+    case 60: cell_body_fit<60, T, PASS, NTMAX>(it.a, l, smem_raw); break;
+    case 64: cell_body_fit<64, T, PASS, NTMAX>(it.a, l, smem_raw); break;
+    case 72: cell_body_fit<72, T, PASS, NTMAX>(it.a, l, smem_raw); break;
+    case 80: cell_body_fit<80, T, PASS, NTMAX>(it.a, l, smem_raw); break;
+    case 96: cell_body_fit<96, T, PASS, NTMAX>(it.a, l, smem_raw); break;
     default: break;
   }
 }

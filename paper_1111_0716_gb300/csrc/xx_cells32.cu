@@ -6,6 +6,8 @@ namespace xx {
 
 cudaError_t launch_cell_pass64(int pass, const CellItems& items, long long ctas, int threads,
                                size_t smem, cudaStream_t s);
+cudaError_t launch_cell_pass32_640(int pass, const CellItems& items, long long ctas, int threads,
+                                   size_t smem, cudaStream_t s);
 
 namespace {
 
@@ -80,6 +82,8 @@ cudaError_t launch_cell_pass(int pass, bool fp64, const CellItems& items, long l
   if (pass < 0 || pass > 3 || ctas <= 0 || ctas > 0x7fffffffLL) return cudaErrorInvalidValue;
   if (fp64) return launch_cell_pass64(pass, items, ctas, threads, smem, s);
   if (threads > kCellThreads32[pass]) return cudaErrorInvalidValue;
+  if ((pass == kCellPassC || pass == kCellPassCT) && threads <= 640)
+    return launch_cell_pass32_640(pass, items, ctas, threads, smem, s);
   switch (pass) {
     case kCellPassA:
       if (smem > 48 * 1024)
