@@ -362,6 +362,17 @@ def test_kept_kernel_tables_change_nothing(gpu, prec):
         assert o[4] == out[0][4]
     assert out[0][5] == 1 and out[2][5] == 1
     assert out[1][5] > wl.nk
+    # a workspace cap whose eighth cannot hold the nk^2 tables: built per batch
+    plan = xx.Plan.from_workload(wl, precision=prec, workspace_cap=1 << 20)
+    plan.set_batch(3, 3)
+    c = gu.dev(wl.c_tgt)
+    plan.profile(True)
+    ex, vx = plan.energy(c, gu.dev(wl.w_occ), c, gu.dev(wl.w_tgt), shared=True)
+    tables = plan.profile_read(reset=True)["kernel_table"][1]
+    plan.sync(timeout_s=600.0)
+    assert tables > wl.nk
+    assert np.array_equal(vx.cpu().numpy(), out[0][0])
+    plan.close()
 
 
 @pytest.mark.parametrize("prec,tol", [(0, gu.FP32_TOL), (1, gu.FP64_TOL)])
