@@ -168,6 +168,12 @@ __device__ __forceinline__ void prefetch_l1(const void* p, long long bytes) {
   if (line < bytes) asm volatile("prefetch.global.L1 [%0];" ::"l"((const char*)p + line));
 }
 
+// The same over the first NT threads, each taking every NT-th line.
+template <int NT> __device__ __forceinline__ void prefetch_l1_all(const void* p, long long bytes) {
+  for (long long line = (long long)threadIdx.x * 128; line < bytes; line += (long long)NT * 128)
+    asm volatile("prefetch.global.L1 [%0];" ::"l"((const char*)p + line));
+}
+
 // Second x step item -> (k1, row).  For A = 8 each half-warp covers four k1
 // values of four consecutive rows (the conflict-free pattern for slot stride S).
 template <int A> __device__ __forceinline__ void x2_item(int it, int& k1, int& row) {
@@ -551,12 +557,17 @@ __device__ __forceinline__ void pass_a_body(const PairArgs& p, int ta, int z, un
 #pragma unroll 1
   for (int tj = 0; tj < p.TJ; ++tj) {
     const C* uj = reinterpret_cast<const C*>(p.u_occ) + tj * p.u_occ_stride + z * plane;
+    const C* uj_next = tj + 1 < p.TJ ? uj + p.u_occ_stride : nullptr;
     C* out = reinterpret_cast<C*>(p.inter) +
              ((long long)(ta * p.TJ + tj) * p.nz + z) * (long long)p.P2 * LX;
+    // once the first x step has read this band's plane, the next band's plane is
+    // prefetched into L1 (measured on GB300 at 96^3: pass A 15.2 -> 13.4 ms per
+    // 64 x 80 launch)
     plane_forward<N, T, DB>(
         tw, s0, s1, p.h1, p.P1, p.h2,
         [&](int y, int x) { return cmulc(uj[y * N + x], ua[y * N + x]); },
-        [&](int kyb, int kxb, C v) { out[kyb * LX + kxb] = v; });
+        [&](int kyb, int kxb, C v) { out[kyb * LX + kxb] = v; },
+        [&] { if (uj_next) prefetch_l1_all<G::NT>(uj_next, plane * (long long)sizeof(C)); });
   }
 }
 template <int N, typename T>
