@@ -290,9 +290,10 @@ def reference_arm(args, rank, world):
               "workload per step" % (n_s, wl.nk * n_s))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": wl.name, "grid": 96, "nk": wl.nk, "n_occ": wl.n_occ,
+            "config": {"workload": wl.name + " (beta-boron-sized rhombohedral cell)", "grid": 96,
+                       "nk": wl.nk, "n_occ": wl.n_occ,
                        "n_tgt": wl.n_tgt, "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
