@@ -76,9 +76,10 @@ __device__ __forceinline__ void cell_body(const PairArgs& a, long long l, unsign
     constexpr bool DB = cell_pass_a_db<N, T>();
     if (threadIdx.x < PlaneCfg<N, T, DB>::NT) pass_a_body<N, T, DB>(a, (int)(l % a.TA), (int)(l / a.TA), smem);
   } else if constexpr (PASS == kCellPassB) {
+    // consecutive CTAs take consecutive f_y rows of one pair, as the single-cell
+    // launch does (its grid is (P2, pairs)), so neighbouring CTAs read neighbouring rows
     constexpr int NTB = 256;
-    const long long pairs = (long long)a.TA * a.TJ;
-    if (threadIdx.x < NTB) pass_b_body<N, NTB, T>(a, (int)(l / pairs), (int)(l % pairs), smem);
+    if (threadIdx.x < NTB) pass_b_body<N, NTB, T>(a, (int)(l % a.P2), (int)(l / a.P2), smem);
   } else if constexpr (PASS == kCellPassC) {
     if (threadIdx.x < PlaneCfg<N, T>::NT) pass_c_body<N, T, false>(a, (int)(l % a.TA), (int)(l / a.TA), smem);
   } else {
