@@ -347,7 +347,7 @@ int xx_sync(xx_plan plan, void *stream, double timeout_s);
                                    per band, issued while the previous band's plane is being
                                    transformed; 0 runs two CTAs per SM reading both planes
                                    with global loads; 1 (default) stages for grid lengths up
-                                   to 64.  Same arithmetic in the same order.  Other values
+                                   to 48.  Same arithmetic in the same order.  Other values
                                    give XX_ERR_INVALID_ARGUMENT. */
 
 #define XX_OPT_TEST_WAIT_EXPIRY 4 /* tests of the failure path only: value != 0 announces the

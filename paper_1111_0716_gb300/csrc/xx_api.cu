@@ -290,7 +290,7 @@ struct xx_plan_s {
   int ta_user = 0, tj_user = 0;
   bool pair_symmetry = true;
   int tma_pass_b = 1;          // XX_OPT_TMA_PASS_B: 0 off, 1 for z length >= 80 with <= 3/4 of a row kept, 2 always
-  int stage_pass_a = 1;        // XX_OPT_STAGE_PASS_A: 0 off, 1 for N <= 64, 2 always
+  int stage_pass_a = 1;        // XX_OPT_STAGE_PASS_A: 0 off, 1 for N <= 48, 2 always
   bool test_wait_expiry = false;   // XX_OPT_TEST_WAIT_EXPIRY
   bool fused_vjp = true;           // XX_OPT_FUSED_VJP
   // XX_OPT_ACC_LIMIT_MB: MiB of FP64 accumulators held for every k-point at once
@@ -681,10 +681,11 @@ PairArgs pair_args(xx_plan p, int TA, int TJ) {
   a.err = p->d_err;
   a.test_wait_expiry = p->test_wait_expiry ? 1 : 0;
   a.nj = TJ;   // one q-point per occupied batch unless the caller sets segments
-  // measured on GB300 (beta cell, 64 targets x 160 occupied x 8 q, pass A): staged
-  // 5.6 % faster at N = 60, 13 % slower at N = 96 (one CTA of 768 threads per SM
-  // against two of 384)
-  a.stage_a = p->prec == XX_FP32_MIXED && (p->stage_pass_a == 2 || (p->stage_pass_a == 1 && p->N <= 64)) ? 1 : 0;
+  // measured on GB300 against the unstaged pass A with its L1 prefetch of the next
+  // occupied plane: the beta step on its 60^3 grid 3.5 % slower staged, the alpha step
+  // (48^3) the same either way, the 96^3 pass A 13 % slower staged (one CTA of 768
+  // threads per SM against two of 384)
+  a.stage_a = p->prec == XX_FP32_MIXED && (p->stage_pass_a == 2 || (p->stage_pass_a == 1 && p->N <= 48)) ? 1 : 0;
   return a;
 }
 
