@@ -175,16 +175,17 @@ def test_every_admissible_grid_gives_the_same_operator(oracle_mod):
 
 def test_anisotropic_grids_give_the_same_operator(oracle_mod):
     """Grids of different lengths per axis, each admissible on its own axis: a
-    sheared cell elongated along a2 (n_max = (4, 6, 4)) on 17 x 25 x 17 (the
-    smallest admissible) and 24 x 32 x 24 gives the same V_x c as on 32^3, and a
-    grid aliasing along the long axis only (32 x 24 x 32) does not."""
+    sheared cell elongated along a2 (n_max = (4, 6, 5)) on 17 x 25 x 21 (the
+    smallest admissible), 24 x 32 x 24 and 18 x 27 x 24 gives the same V_x c as on
+    32^3, and a grid aliasing along the long axis only (32 x 23 x 32) does not."""
     lat = np.array([[10.0, 0.0, 0.0], [1.5, 13.3, 0.0], [0.8, -1.1, 10.0]])
     wl = synth.make_workload("sheared", lat, (32, 32, 32), np.zeros((1, 3)), math.pi, 3, 4,
                              [1.0, 0.8, 0.5], 41)
     nm = wl.n_max()
     assert nm[1] > nm[0] and nm[1] > nm[2]
     ref = oracle_mod.apply(wl)
-    for g in ((4 * nm[0] + 1, 4 * nm[1] + 1, 4 * nm[2] + 1), (24, 32, 24)):
+    assert tuple(int(v) for v in nm) == (4, 6, 5)
+    for g in ((4 * nm[0] + 1, 4 * nm[1] + 1, 4 * nm[2] + 1), (24, 32, 24), (18, 27, 24)):
         vx = oracle_mod.apply(wl.replace(grid=tuple(int(v) for v in g)))
         assert np.abs(vx - ref).max() <= 1e-12 * np.abs(ref).max()
     aliased = oracle_mod.apply(wl.replace(grid=(32, 4 * int(nm[1]) - 1, 32)))
