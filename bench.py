@@ -309,6 +309,24 @@ def profile_case(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_1111_0716_gb300 import synth, xx
+    if args.profile_alpha:
+        wa = synth.alpha_boron()
+        plan = xx.Plan.from_workload(wa, precision=xx.XX_FP32_MIXED)
+        c = torch.from_numpy(wa.c_tgt).cuda()
+        wo, wt = torch.from_numpy(wa.w_occ).cuda(), torch.from_numpy(wa.w_tgt).cuda()
+        l0 = 0
+        for step in range(2):
+            if step == 1:
+                l0 = plan.info()["kernel_launches"]
+            plan.energy(c, wo, c, wt, shared=True)
+        torch.cuda.synchronize()
+        info = plan.info()
+        plan.close()
+        print(json.dumps({"profile_case": wa.name, "pairs_per_step": wa.pair_count(),
+                          "launches_first_step": l0, "launches_second_step": info["kernel_launches"] - l0,
+                          "batch": [info["targets_per_batch"], info["occupied_per_batch"]],
+                          "q_per_batch": info["q_per_batch"]}))
+        return
     wl = synth.beta_boron()
     if args.profile_grid:
         wl = wl.replace(grid=(args.profile_grid,) * 3)
@@ -520,6 +538,10 @@ def main():
     ap.add_argument("--profile-grid", type=int, default=0,
                     help="with --profile-case: run the case on this FFT grid instead of 96^3 "
                          "(any supported length >= 4 n_max + 1 = 57, e.g. 60)")
+    ap.add_argument("--profile-alpha", action="store_true",
+                    help="with --profile-case: two steps of the alpha-boron-sized workload (48^3, "
+                         "64 k-points) through xx_energy with shared grids, the first of which "
+                         "builds the grids and kernel tables")
     ap.add_argument("--with-vjp", action="store_true",
                     help="also time the vector-Jacobian product (xx_apply_vjp, both orbital "
                          "sets) on 16 target bands of every k-point")
