@@ -71,3 +71,32 @@ def test_sharded_plan_refuses_unsharded_derivatives(gpu):
     with pytest.raises(xx.XXError):
         plan.set_shard(2, 2)
     plan.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 8])
+@pytest.mark.parametrize("batch", [(3, 3), None])
+def test_bench_schedule_model_matches_sharded_plans(gpu, n, batch):
+    """bench.py checks its launch-schedule model against each rank's transform count;
+    the model with the library's block assignment must give every shard's count, with
+    one q-point per batch and with the default multi-q batches."""
+    torch, xx = gpu
+    import bench
+    wl = rhombo24()
+    owner = xx.xx_shard_blocks(wl.nk, wl.n_occ, wl.n_tgt, n)
+    for r in range(n):
+        plan = xx.Plan.from_workload(wl, precision=0)
+        if batch:
+            plan.set_batch(*batch)
+        plan.set_shard(r, n)
+        c = gu.dev(wl.c_tgt)
+        plan.energy(c, gu.dev(wl.w_occ), c, gu.dev(wl.w_tgt), shared=True)
+        plan.sync(timeout_s=600.0)
+        info = plan.info()
+        plan.close()
+
+        def owned(k, q, r=r):
+            k, q = min(k, q), max(k, q)
+            return owner[k * wl.nk - k * (k - 1) // 2 + (q - k)] == r
+        sched = bench.batch_schedule(wl.nk, wl.n_occ, wl.n_tgt, info["targets_per_batch"],
+                                     info["occupied_per_batch"], info["q_per_batch"], owned=owned)
+        assert sum(ta * tj for _, ta, tj in sched) == info["pairs_transformed"]
